@@ -1,0 +1,401 @@
+// Node-contraction engine. Every hot-path contraction around one node t of <bra| W |ket> with
+// environments on some legs is lowered to the same pipeline of batched GEMMs (ket first):
+//
+//   T_0     = ket_t permuted to [b_C1][b_C2..b_Cm][q][b_open]         (contracted legs first)
+//   T_l     = sum_b T_{l-1}[b][rest] E_Cl[w][a][b]  -> [rest][a_Cl]     l = 1..m, one item per
+//             distinct prefix (w_C1..w_Cl) of the TTNO entries (shared between entries)
+//   Z[slot] = sum_{groups g of slot} sum_q T_m[prefix_g][q][rest] O_g[p][q]  -> [rest][p]
+//             where O_g = sum of c_e * op_e over the entries with that prefix and open-leg
+//             value (one combined d x d operator per group)
+//   closure: env  E_open[slot][a][b] = sum_rest bra_t[a][rest] Z[slot][b][rest]
+//            scalar <bra|H|ket>       = sum bra_t * Z
+//            local  (H_eff x)         = Z
+//
+// This is the contraction order "absorb the ket into the environments leg by leg, apply the
+// local operators, close with the bra" of Sec. II.C (Figs. variational and als), with the TTNO
+// kept block-sparse: only distinct (w-prefix) and (prefix, w_open) combinations are contracted.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+
+namespace {
+
+long long key_of(int node, int open) { return (long long)node * 64 + (open + 1); }
+
+}  // namespace
+
+NodePlan& get_plan(ttn_ttno* H, int t, int open) {
+  const long long key = key_of(t, open);
+  auto it = H->plans.find(key);
+  if (it != H->plans.end()) return it->second;
+  NodePlan p;
+  p.node = t;
+  p.open = open;
+  const int nl = H->tree.nlegs(t);
+  for (int m = 0; m < nl; ++m)
+    if (m != open) p.C.push_back(m);
+  const int mC = (int)p.C.size();
+  p.n_slots = open >= 0 ? H->wdim(t, open) : 1;
+  const int d = H->tree.d(t);
+  std::vector<std::map<std::vector<int>, int>> pref(mC + 1);
+  p.level.resize(mC);
+  struct G {
+    int prefix, slot;
+    std::vector<double> op;
+  };
+  std::vector<G> groups;
+  std::map<std::pair<int, int>, int> gidx;
+  for (const TtnoEntry& e : H->entries[t]) {
+    std::vector<int> key;
+    int par = 0;
+    for (int l = 0; l < mC; ++l) {
+      key.push_back(e.w[p.C[l]]);
+      auto ins = pref[l + 1].emplace(key, (int)pref[l + 1].size());
+      if (ins.second) p.level[l].push_back({par, e.w[p.C[l]]});
+      par = ins.first->second;
+    }
+    const int slot = open >= 0 ? e.w[open] : 0;
+    auto gi = gidx.emplace(std::make_pair(par, slot), (int)groups.size());
+    if (gi.second) groups.push_back({par, slot, std::vector<double>((size_t)d * d, 0.0)});
+    std::vector<double>& O = groups[gi.first->second].op;
+    const double* src = H->op_data.data() + H->op_off[e.op];
+    for (int i = 0; i < d * d; ++i) O[i] += e.coef * src[i];
+  }
+  std::stable_sort(groups.begin(), groups.end(),
+                   [](const G& a, const G& b) { return a.slot < b.slot; });
+  p.slot_ptr.assign(p.n_slots + 1, 0);
+  for (const G& g : groups) {
+    p.grp_prefix.push_back(g.prefix);
+    p.slot_ptr[g.slot + 1]++;
+    p.ocomb.insert(p.ocomb.end(), g.op.begin(), g.op.end());
+  }
+  for (int s = 0; s < p.n_slots; ++s) p.slot_ptr[s + 1] += p.slot_ptr[s];
+  cudaStream_t st = H->ctx->stream;
+  const size_t no = std::max<size_t>(p.ocomb.size(), 1);
+  p.d_ocomb64 = DevBuf(no * sizeof(double), st);
+  p.d_ocomb32 = DevBuf(no * sizeof(float), st);
+  std::vector<float> o32(p.ocomb.begin(), p.ocomb.end());
+  if (!p.ocomb.empty()) {
+    CUDA_CHECK(cudaMemcpyAsync(p.d_ocomb64.p, p.ocomb.data(), p.ocomb.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(p.d_ocomb32.p, o32.data(), o32.size() * sizeof(float),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+  }
+  return H->plans.emplace(key, std::move(p)).first->second;
+}
+
+namespace {
+
+// Item tables (per stage: C offset per item, CSR of segments with A/B offsets) of one plan for
+// concrete bond dimensions; cached in the TTNO.
+DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da,
+                      const std::vector<int>& Db, int d, int out_kind,
+                      std::vector<long long>& sizes) {
+  const int mC = (int)p.C.size();
+  const int nl = (int)Da.size();
+  sizes.assign(mC + 1, 0);
+  long long sz = d;
+  for (int m = 0; m < nl; ++m) sz *= Db[m];
+  sizes[0] = sz;
+  for (int l = 1; l <= mC; ++l) {
+    const int c = p.C[l - 1];
+    sizes[l] = sizes[l - 1] / Db[c] * Da[c];
+  }
+  std::vector<long long> key = {p.node, p.open, d, out_kind};
+  key.insert(key.end(), Da.begin(), Da.end());
+  key.insert(key.end(), Db.begin(), Db.end());
+  auto it = H->tables.find(key);
+  if (it != H->tables.end()) return it->second;
+
+  using HostStage = StageHost;
+  std::vector<HostStage> hs;
+  for (int l = 1; l <= mC; ++l) {
+    HostStage s;
+    const int c = p.C[l - 1];
+    const long long eslice = (long long)Da[c] * Db[c];
+    for (size_t j = 0; j < p.level[l - 1].size(); ++j) {
+      const auto& pr = p.level[l - 1][j];
+      s.seg_a.push_back(l == 1 ? 0 : (long long)pr.first * sizes[l - 1]);
+      s.seg_b.push_back((long long)pr.second * eslice);
+      s.seg_ptr.push_back((int)s.seg_a.size());
+      s.sub_c.push_back((long long)j * sizes[l]);
+    }
+    hs.push_back(std::move(s));
+  }
+  {
+    HostStage s;
+    const long long zsize = sizes[mC];
+    for (int slot = 0; slot < p.n_slots; ++slot) {
+      for (int g = p.slot_ptr[slot]; g < p.slot_ptr[slot + 1]; ++g) {
+        s.seg_a.push_back(mC == 0 ? 0 : (long long)p.grp_prefix[g] * sizes[mC]);
+        s.seg_b.push_back((long long)g * d * d);
+      }
+      s.seg_ptr.push_back((int)s.seg_a.size());
+      s.sub_c.push_back((long long)slot * zsize);
+    }
+    hs.push_back(std::move(s));
+  }
+  if (out_kind == OUT_ENV) {
+    HostStage s;
+    const int o = p.open;
+    const long long zsize = sizes[mC];
+    for (int slot = 0; slot < p.n_slots; ++slot) {
+      s.seg_a.push_back(0);
+      s.seg_b.push_back((long long)slot * zsize);
+      s.seg_ptr.push_back((int)s.seg_a.size());
+      s.sub_c.push_back((long long)slot * Da[o] * Db[o]);
+    }
+    hs.push_back(std::move(s));
+  }
+  // pack into one device buffer
+  size_t bytes = 0;
+  for (auto& s : hs) {
+    bytes += (s.sub_c.size() + s.seg_a.size() + s.seg_b.size()) * sizeof(long long);
+    bytes += s.seg_ptr.size() * sizeof(int) + 64;   // + alignment of 4 arrays
+  }
+  std::vector<char> host(bytes + 64, 0);
+  DevTables t;
+  t.buf = DevBuf(bytes + 64, H->ctx->stream);
+  size_t off = 0;
+  char* dbase = static_cast<char*>(t.buf.p);
+  auto put = [&](const void* src, size_t n) -> const void* {
+    off = (off + 15) & ~size_t(15);
+    if (n) std::memcpy(host.data() + off, src, n);
+    const void* dp = dbase + off;
+    off += n;
+    return dp;
+  };
+  for (auto& s : hs) {
+    StageDev ds;
+    ds.n_sub = (int)s.sub_c.size();
+    ds.sub_c = (const long long*)put(s.sub_c.data(), s.sub_c.size() * sizeof(long long));
+    ds.seg_ptr = (const int*)put(s.seg_ptr.data(), s.seg_ptr.size() * sizeof(int));
+    ds.seg_a = (const long long*)put(s.seg_a.data(), s.seg_a.size() * sizeof(long long));
+    ds.seg_b = (const long long*)put(s.seg_b.data(), s.seg_b.size() * sizeof(long long));
+    t.stages.push_back(ds);
+  }
+  t.host = hs;
+  CUDA_CHECK(cudaMemcpyAsync(t.buf.p, host.data(), off, cudaMemcpyHostToDevice, H->ctx->stream));
+  CUDA_CHECK(cudaStreamSynchronize(H->ctx->stream));
+  return H->tables.emplace(key, std::move(t)).first->second;
+}
+
+}  // namespace
+
+template <>
+const double* block_node<double>(const ttn_block* b, int t) {
+  return b->node64(t);
+}
+template <>
+const float* block_node<float>(const ttn_block* b, int t) {
+  return b->node32(t);
+}
+
+template <class T>
+void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
+             const ttn_block* ket, const PairSet& ps, const std::vector<const T*>& env,
+             const std::vector<int>& env_da, void* out, long long out_len, int out_kind) {
+  const int P = ps.P;
+  const int* d_pb = ps.d_pb;
+  const int* d_pk = ps.d_pk;
+  const TreeInfo& tr = H->tree;
+  const int nl = tr.nlegs(t), d = tr.d(t);
+  NodePlan& p = get_plan(H, t, open);
+  const int mC = (int)p.C.size();
+  std::vector<int> Da(nl), Db(nl), Dw(nl);
+  for (int m = 0; m < nl; ++m) {
+    Db[m] = ket->bdim(t, m);
+    Dw[m] = H->wdim(t, m);
+    Da[m] = bra ? bra->bdim(t, m) : env_da[m];
+  }
+  std::vector<long long> sizes;
+  DevTables& tab = get_tables(H, p, Da, Db, d, out_kind, sizes);
+  cudaStream_t st = ctx->stream;
+
+  // T_0: permuted ket of every ket state
+  std::vector<int> kd(Db.begin(), Db.end());
+  kd.push_back(d);
+  std::vector<int> perm(p.C.begin(), p.C.end());
+  perm.push_back(nl);
+  if (open >= 0) perm.push_back(open);
+  const long long ksize = ket->size[t];
+  DevBuf kp((size_t)ket->n_states * ksize * sizeof(T), st);
+  launch_permute<T>(ctx, block_node<T>(ket, t), kp.as<T>(), ket->n_states, nl + 1, kd.data(),
+                    perm.data());
+
+  const void* prev = kp.p;
+  long long prev_len = (long long)ket->n_states * ksize;
+  int prev_mode = MODE_KET;
+  long long prev_pstride = ksize;
+  std::vector<DevBuf> Tl(mC + 1);
+  for (int l = 1; l <= mC; ++l) {
+    const int c = p.C[l - 1];
+    const long long rest = sizes[l - 1] / Db[c];
+    const int nsub = (int)p.level[l - 1].size();
+    Tl[l] = DevBuf((size_t)P * nsub * sizes[l] * sizeof(T), st);
+    GemmDesc g{};
+    g.M = (int)rest;
+    g.N = Da[c];
+    g.K = Db[c];
+    g.a_sm = 1;
+    g.a_sk = rest;
+    g.b_sn = Db[c];
+    g.b_sk = 1;
+    g.c_sm = Da[c];
+    g.c_sn = 1;
+    g.A = {prev, prev_mode, prev_pstride};
+    g.B = {env[c], MODE_PAIR, (long long)Dw[c] * Da[c] * Db[c]};
+    g.C = Tl[l].p;
+    g.c_mode = MODE_PAIR;
+    g.c_pstride = (long long)nsub * sizes[l];
+    g.n_pairs = P;
+    g.pair_bra = d_pb;
+    g.pair_ket = d_pk;
+    g.st = tab.stages[l - 1];
+    g.hst = &tab.host[l - 1];
+    g.a_len = l == 1 ? (long long)ket->n_states * ksize : prev_len;
+    g.b_len = (long long)P * Dw[c] * Da[c] * Db[c];
+    g.c_len = (long long)P * g.c_pstride;
+    g.max_bra = ps.max_bra;
+    g.max_ket = ps.max_ket;
+    launch_gemm<T>(ctx, g);
+    prev_len = g.c_len;
+    prev = Tl[l].p;
+    prev_mode = MODE_PAIR;
+    prev_pstride = g.c_pstride;
+  }
+
+  const long long zsize = sizes[mC];
+  const long long zrest = zsize / d;
+  DevBuf zbuf;
+  void* Z = out;
+  if (out_kind != OUT_LOCAL) {
+    zbuf = DevBuf((size_t)P * p.n_slots * zsize * sizeof(T), st);
+    Z = zbuf.p;
+  }
+  {
+    GemmDesc g{};
+    g.M = (int)zrest;
+    g.N = d;
+    g.K = d;
+    g.a_sm = 1;
+    g.a_sk = zrest;
+    g.b_sn = d;
+    g.b_sk = 1;
+    g.c_sm = d;
+    g.c_sn = 1;
+    g.A = {prev, prev_mode, prev_pstride};
+    const void* oc = sizeof(T) == 8 ? p.d_ocomb64.p : p.d_ocomb32.p;
+    g.B = {oc, MODE_CONST, 0};
+    g.C = Z;
+    g.c_mode = MODE_PAIR;
+    g.c_pstride = (long long)p.n_slots * zsize;
+    g.n_pairs = P;
+    g.pair_bra = d_pb;
+    g.pair_ket = d_pk;
+    g.st = tab.stages[mC];
+    g.hst = &tab.host[mC];
+    g.a_len = prev_len;
+    g.b_len = std::max<long long>((long long)p.ocomb.size(), 1);
+    g.c_len = out_kind == OUT_LOCAL ? out_len : (long long)P * g.c_pstride;
+    g.max_bra = ps.max_bra;
+    g.max_ket = ps.max_ket;
+    launch_gemm<T>(ctx, g);
+  }
+
+  if (out_kind == OUT_ENV) {
+    std::vector<int> bd(Da.begin(), Da.end());
+    bd.push_back(d);
+    std::vector<int> bperm = {open};
+    bperm.insert(bperm.end(), p.C.begin(), p.C.end());
+    bperm.push_back(nl);
+    const long long bsize = bra->size[t];
+    DevBuf bp((size_t)bra->n_states * bsize * sizeof(T), st);
+    launch_permute<T>(ctx, block_node<T>(bra, t), bp.as<T>(), bra->n_states, nl + 1, bd.data(),
+                      bperm.data());
+    const long long K = zsize / Db[open];
+    GemmDesc g{};
+    g.M = Da[open];
+    g.N = Db[open];
+    g.K = (int)K;
+    g.a_sm = K;
+    g.a_sk = 1;
+    g.b_sn = K;
+    g.b_sk = 1;
+    g.c_sm = Db[open];
+    g.c_sn = 1;
+    g.A = {bp.p, MODE_BRA, bsize};
+    g.B = {Z, MODE_PAIR, (long long)p.n_slots * zsize};
+    g.C = out;
+    g.c_mode = MODE_PAIR;
+    g.c_pstride = (long long)p.n_slots * Da[open] * Db[open];
+    g.n_pairs = P;
+    g.pair_bra = d_pb;
+    g.pair_ket = d_pk;
+    g.st = tab.stages[mC + 1];
+    g.hst = &tab.host[mC + 1];
+    g.a_len = (long long)bra->n_states * bsize;
+    g.b_len = (long long)P * p.n_slots * zsize;
+    g.c_len = out_len;
+    g.max_bra = ps.max_bra;
+    g.max_ket = ps.max_ket;
+    launch_gemm<T>(ctx, g);
+  } else if (out_kind == OUT_SCALAR) {
+    TTN_REQUIRE(zsize == bra->size[t] && out_len >= P, "scalar closure: shape mismatch");
+    launch_pair_dot<T>(ctx, block_node<T>(bra, t), bra->size[t], static_cast<const T*>(Z), zsize,
+                       zsize, P, d_pb, static_cast<double*>(out), ps.max_bra,
+                       (long long)bra->n_states * bra->size[t], (long long)P * zsize);
+  }
+}
+
+template <class T>
+void envs_compute(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                  const PairSet& ps, int direction, std::vector<DevBuf>& up,
+                  std::vector<DevBuf>& down) {
+  const int P = ps.P;
+  const TreeInfo& tr = H->tree;
+  up.resize(tr.n);
+  down.resize(tr.n);
+  cudaStream_t st = ctx->stream;
+  auto esize = [&](int c) {
+    return (long long)H->wbond[c] * bra->bond[c] * ket->bond[c];
+  };
+  for (int t : tr.post) {
+    if (t == tr.root) continue;
+    const int nl = tr.nlegs(t);
+    std::vector<const T*> env(nl, nullptr);
+    for (int m = 1; m < nl; ++m) env[m] = up[tr.legs[t][m]].as<T>();
+    up[t] = DevBuf((size_t)P * esize(t) * sizeof(T), st);
+    node_op<T>(ctx, H, t, 0, bra, ket, ps, env, {}, up[t].p, (long long)P * esize(t), OUT_ENV);
+  }
+  if (direction == 0) return;
+  for (int u : tr.pre) {
+    const int nl = tr.nlegs(u);
+    const int off = u == tr.root ? 0 : 1;
+    for (int m = off; m < nl; ++m) {
+      const int c = tr.legs[u][m];
+      std::vector<const T*> env(nl, nullptr);
+      if (off) env[0] = down[u].as<T>();
+      for (int m2 = off; m2 < nl; ++m2)
+        if (m2 != m) env[m2] = up[tr.legs[u][m2]].as<T>();
+      down[c] = DevBuf((size_t)P * esize(c) * sizeof(T), st);
+      node_op<T>(ctx, H, u, m, bra, ket, ps, env, {}, down[c].p, (long long)P * esize(c),
+                 OUT_ENV);
+    }
+  }
+}
+
+template void node_op<double>(ttn_ctx*, ttn_ttno*, int, int, const ttn_block*, const ttn_block*,
+                              const PairSet&, const std::vector<const double*>&,
+                              const std::vector<int>&, void*, long long, int);
+template void node_op<float>(ttn_ctx*, ttn_ttno*, int, int, const ttn_block*, const ttn_block*,
+                             const PairSet&, const std::vector<const float*>&,
+                             const std::vector<int>&, void*, long long, int);
+template void envs_compute<double>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
+                                   const PairSet&, int, std::vector<DevBuf>&,
+                                   std::vector<DevBuf>&);
+template void envs_compute<float>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
+                                  const PairSet&, int, std::vector<DevBuf>&,
+                                  std::vector<DevBuf>&);

@@ -1,0 +1,255 @@
+// Internal declarations of libttn (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ttn.h"
+
+// ------------------------------------------------------------------------------------------------
+// errors: internal code throws TtnError; every extern "C" entry point converts it to a status.
+// ------------------------------------------------------------------------------------------------
+struct TtnError {
+  ttn_status st;
+  std::string msg;
+};
+
+std::string ttn_fmt(const char* f, ...);
+#define TTN_FAIL(st, ...) throw TtnError{(st), ttn_fmt(__VA_ARGS__)}
+#define TTN_REQUIRE(cond, ...) \
+  do {                         \
+    if (!(cond)) TTN_FAIL(TTN_EINVAL, __VA_ARGS__); \
+  } while (0)
+#define CUDA_CHECK(x)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      TTN_FAIL(e_ == cudaErrorMemoryAllocation ? TTN_ENOMEM : TTN_ECUDA, "%s: %s (%s:%d)", \
+               #x, cudaGetErrorString(e_), __FILE__, __LINE__);                           \
+  } while (0)
+#define CUDA_LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
+
+// ------------------------------------------------------------------------------------------------
+// tree
+// ------------------------------------------------------------------------------------------------
+struct TreeInfo {
+  int n = 0, root = -1;
+  std::vector<int> parent, phys;            // phys = 0 for auxiliary nodes
+  std::vector<std::vector<int>> children;   // increasing index order
+  std::vector<std::vector<int>> legs;       // neighbour of each leg: parent first, then children
+  std::vector<int> pre, post;               // depth-first pre-/post-order from the root
+  int d(int i) const { return phys[i] > 0 ? phys[i] : 1; }
+  int nlegs(int i) const { return (int)legs[i].size(); }
+  int leg_to(int i, int nb) const {
+    for (int m = 0; m < nlegs(i); ++m)
+      if (legs[i][m] == nb) return m;
+    return -1;
+  }
+  std::vector<int> path(int u, int v) const;   // nodes from u to v inclusive
+  bool same_shape(const TreeInfo& o) const { return parent == o.parent && phys == o.phys; }
+};
+
+TreeInfo make_tree(int n, const int* parent, const int* phys);
+
+struct ttn_ctx;
+struct ttn_tree {
+  ttn_ctx* ctx = nullptr;
+  TreeInfo info;
+};
+
+// ------------------------------------------------------------------------------------------------
+// device memory: stream-ordered allocations from the device's default pool
+// ------------------------------------------------------------------------------------------------
+struct ttn_ctx;
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t s = 0;
+  DevBuf() = default;
+  DevBuf(size_t n, cudaStream_t st);
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept;
+  ~DevBuf();
+  void reset();
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct ttn_ctx {
+  int device = 0;
+  cudaStream_t stream = 0;
+  bool own_stream = false;
+  std::string last_error;
+  long long launches = 0;
+};
+
+// ------------------------------------------------------------------------------------------------
+// TTNO
+// ------------------------------------------------------------------------------------------------
+struct TtnoEntry {
+  int w[TTN_MAX_LEGS];
+  int op;        // index into the op table
+  double coef;
+};
+
+// Symbolic plan of one node contraction with one open leg (or none): the prefix tries over
+// the contracted legs and the per-output-slot groups with their combined local operators.
+struct NodePlan {
+  int node = -1, open = -1;
+  std::vector<int> C;                                  // contracted legs in order
+  std::vector<std::vector<std::pair<int, int>>> level; // level[l]: (parent prefix, w) per prefix
+  int n_slots = 1;
+  std::vector<int> grp_prefix;                         // per group (sorted by slot)
+  std::vector<int> slot_ptr;                           // CSR over slots
+  std::vector<double> ocomb;                           // per group: d x d  sum_e c_e O_e
+  DevBuf d_ocomb64, d_ocomb32;
+};
+
+// Item tables of one GEMM stage: per item ("sub") the C offset and a CSR list of segments,
+// each with its own A and B offsets (device copy for the kernel, host copy for bounds checks).
+struct StageDev {
+  int n_sub = 0;
+  const long long* sub_c = nullptr;
+  const int* seg_ptr = nullptr;
+  const long long* seg_a = nullptr;
+  const long long* seg_b = nullptr;
+};
+struct StageHost {
+  std::vector<long long> sub_c, seg_a, seg_b;
+  std::vector<int> seg_ptr{0};
+};
+struct DevTables {
+  DevBuf buf;   // all item tables of one (plan, dims) in one allocation
+  std::vector<StageDev> stages;
+  std::vector<StageHost> host;
+};
+
+struct ttn_ttno {
+  ttn_ctx* ctx = nullptr;
+  TreeInfo tree;
+  std::vector<int> wbond;
+  std::vector<int> op_node;
+  std::vector<long long> op_off;
+  std::vector<double> op_data;
+  std::vector<std::vector<TtnoEntry>> entries;
+  std::map<long long, NodePlan> plans;
+  std::map<std::vector<long long>, DevTables> tables;
+  int wdim(int node, int leg) const {
+    int nb = tree.legs[node][leg];
+    return tree.parent[node] == nb ? wbond[node] : wbond[nb];
+  }
+};
+
+NodePlan& get_plan(ttn_ttno* H, int node, int open);
+ttn_ttno* identity_ttno(ttn_ctx* ctx, const TreeInfo& tree);
+
+// ------------------------------------------------------------------------------------------------
+// blocks and environments
+// ------------------------------------------------------------------------------------------------
+struct ttn_block {
+  ttn_ctx* ctx = nullptr;
+  TreeInfo tree;
+  int n_states = 0;
+  std::vector<int> bond;                      // per node (edge to parent)
+  std::vector<std::vector<int>> dims;         // per node: leg dims then physical (1 for aux)
+  std::vector<long long> size, off;           // per node: tensor size, slab offset
+  long long total = 0;
+  DevBuf d64;
+  mutable DevBuf d32;
+  mutable bool f32_valid = false;
+  int bdim(int node, int leg) const {
+    int nb = tree.legs[node][leg];
+    return tree.parent[node] == nb ? bond[node] : bond[nb];
+  }
+  double* node64(int t) const { return d64.as<double>() + off[t]; }
+  const float* node32(int t) const;           // refreshes the float mirror if stale
+  void touch() { f32_valid = false; }
+};
+
+struct ttn_envs {
+  ttn_ctx* ctx = nullptr;
+  TreeInfo tree;
+  int n_pairs = 0;
+  int prec = TTN_FP64;
+  bool has_up = false, has_down = false;
+  std::vector<int> Dw, Da, Db;                // per edge (child node)
+  std::vector<DevBuf> up, down;               // per edge: [pair][w][a][b]
+  std::vector<int> pair_bra, pair_ket;
+  const ttn_ttno* H = nullptr;
+  long long esize(int t) const { return (long long)Dw[t] * Da[t] * Db[t]; }
+};
+
+// ------------------------------------------------------------------------------------------------
+// kernels (kernels.cu)
+// ------------------------------------------------------------------------------------------------
+enum { MODE_PAIR = 0, MODE_BRA = 1, MODE_KET = 2, MODE_CONST = 3 };
+
+struct GemmOperand {
+  const void* base;
+  int mode;
+  long long pstride;
+};
+
+struct GemmDesc {
+  int M, N, K;
+  long long a_sm, a_sk, b_sn, b_sk, c_sm, c_sn;
+  GemmOperand A, B;
+  void* C;
+  int c_mode;
+  long long c_pstride;
+  int n_pairs;
+  const int* pair_bra;
+  const int* pair_ket;
+  StageDev st;
+  // host-side launch validation (never read on the device)
+  const StageHost* hst;
+  long long a_len, b_len, c_len;   // elements addressable from each base pointer
+  int max_bra, max_ket;            // largest state index in pair_bra / pair_ket
+};
+
+// A list of (bra, ket) pairs on the device plus the host facts the bounds checks need.
+struct PairSet {
+  int P = 0;
+  const int* d_pb = nullptr;
+  const int* d_pk = nullptr;
+  int max_bra = 0, max_ket = 0;
+};
+
+template <class T> void launch_gemm(ttn_ctx* ctx, const GemmDesc& g);
+template <class T>
+void launch_permute(ttn_ctx* ctx, const T* in, T* out, long long batch, int nd, const int* dims,
+                    const int* perm);
+template <class T>
+void launch_pair_dot(ttn_ctx* ctx, const T* bra, long long bra_stride, const T* Z,
+                     long long z_stride, long long n, int n_pairs, const int* pair_bra,
+                     double* out, int max_bra, long long bra_len, long long z_len);
+template <class T>
+void launch_shift_axpy(ttn_ctx* ctx, T* y, const T* x, const double* shift, int n_states,
+                       long long size);
+void launch_to_f32(ttn_ctx* ctx, const double* in, float* out, long long n);
+void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n);
+void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* pb,
+                         const int* pk, int symmetric, double* out, int ld);
+
+// ------------------------------------------------------------------------------------------------
+// engine (engine.cu)
+// ------------------------------------------------------------------------------------------------
+enum { OUT_ENV = 0, OUT_SCALAR = 1, OUT_LOCAL = 2 };
+
+template <class T>
+void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
+             const ttn_block* ket, const PairSet& ps, const std::vector<const T*>& env,
+             const std::vector<int>& env_da, void* out, long long out_len, int out_kind);
+
+template <class T>
+void envs_compute(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                  const PairSet& ps, int direction, std::vector<DevBuf>& up,
+                  std::vector<DevBuf>& down);
+
+template <class T> const T* block_node(const ttn_block* b, int t);

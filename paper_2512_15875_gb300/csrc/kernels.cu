@@ -1,0 +1,354 @@
+// Generic device kernels of the contraction engine: a strided batched GEMM with per-item
+// segment sums (the workhorse of every node contraction), tensor permutes, per-pair dots.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <class T>
+__device__ __forceinline__ const T* operand_base(const GemmOperand& o, int pair, const int* pb,
+                                                 const int* pk) {
+  long long idx = 0;
+  if (o.mode == MODE_PAIR) idx = pair;
+  else if (o.mode == MODE_BRA) idx = pb[pair];
+  else if (o.mode == MODE_KET) idx = pk[pair];
+  return static_cast<const T*>(o.base) + idx * o.pstride;
+}
+
+// One CTA computes a BM x BN tile of one item (pair, sub) of
+//   C[item](m, n) = sum_{segments s of sub} sum_k A_s(m, k) * B_s(n, k)
+// with arbitrary element strides. Shared-memory tiles are stored k-major; each thread owns a
+// TM x TN register tile with rows/columns strided by BM/TM and BN/TN (conflict-free reads).
+template <class T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(kThreads) gemm_kernel(GemmDesc g, int tiles_m, int tiles_n) {
+  static_assert((BM / TM) * (BN / TN) == kThreads, "tile/thread mismatch");
+  __shared__ T As[BK][BM];
+  __shared__ T Bs[BK][BN];
+  const long long tiles = (long long)tiles_m * tiles_n;
+  const long long bid = blockIdx.x;
+  const int tile = (int)(bid % tiles);
+  const long long rest = bid / tiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const int m0 = (tile / tiles_n) * BM;
+  const int n0 = (tile % tiles_n) * BN;
+  const T* Ab = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket);
+  const T* Bb = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket);
+  const int tid = threadIdx.x;
+  const int ty = tid / (BN / TN), tx = tid % (BN / TN);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  const int s_begin = g.st.seg_ptr[sub], s_end = g.st.seg_ptr[sub + 1];
+  for (int s = s_begin; s < s_end; ++s) {
+    const T* Ap = Ab + g.st.seg_a[s];
+    const T* Bp = Bb + g.st.seg_b[s];
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+      if (g.a_sm == 1) {
+        for (int i = tid; i < BM * BK; i += kThreads) {
+          const int m = i % BM, k = i / BM, gm = m0 + m, gk = k0 + k;
+          As[k][m] = (gm < g.M && gk < g.K) ? Ap[gm + (long long)gk * g.a_sk] : T(0);
+        }
+      } else {
+        for (int i = tid; i < BM * BK; i += kThreads) {
+          const int k = i % BK, m = i / BK, gm = m0 + m, gk = k0 + k;
+          As[k][m] = (gm < g.M && gk < g.K) ? Ap[(long long)gm * g.a_sm + (long long)gk * g.a_sk]
+                                            : T(0);
+        }
+      }
+      if (g.b_sn == 1) {
+        for (int i = tid; i < BN * BK; i += kThreads) {
+          const int n = i % BN, k = i / BN, gn = n0 + n, gk = k0 + k;
+          Bs[k][n] = (gn < g.N && gk < g.K) ? Bp[gn + (long long)gk * g.b_sk] : T(0);
+        }
+      } else {
+        for (int i = tid; i < BN * BK; i += kThreads) {
+          const int k = i % BK, n = i / BK, gn = n0 + n, gk = k0 + k;
+          Bs[k][n] = (gn < g.N && gk < g.K) ? Bp[(long long)gn * g.b_sn + (long long)gk * g.b_sk]
+                                            : T(0);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        T a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[k][ty + i * (BM / TM)];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[k][tx + j * (BN / TN)];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  T* Cb = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gm = m0 + ty + i * (BM / TM);
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx + j * (BN / TN);
+      if (gn < g.N) Cb[(long long)gm * g.c_sm + (long long)gn * g.c_sn] = acc[i][j];
+    }
+  }
+}
+
+struct TileCfg {
+  int bm, bn;
+};
+constexpr TileCfg kCfgs[] = {{64, 64}, {64, 32}, {32, 32}, {128, 16}, {64, 16}, {16, 16}};
+
+template <class T>
+void dispatch(int cfg, const GemmDesc& g, int tm, int tn, long long grid, cudaStream_t s) {
+  switch (cfg) {
+    case 0: gemm_kernel<T, 64, 64, 16, 4, 4><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+    case 1: gemm_kernel<T, 64, 32, 16, 4, 2><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+    case 2: gemm_kernel<T, 32, 32, 16, 2, 2><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+    case 3: gemm_kernel<T, 128, 16, 16, 8, 1><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+    case 4: gemm_kernel<T, 64, 16, 16, 4, 1><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+    default: gemm_kernel<T, 16, 16, 16, 1, 1><<<grid, kThreads, 0, s>>>(g, tm, tn); break;
+  }
+}
+
+struct PermArgs {
+  int nd;
+  long long od[8];   // output dims
+  long long is[8];   // input stride of the input axis placed at each output position
+};
+
+template <class T>
+__global__ void permute_kernel(const T* __restrict__ in, T* __restrict__ out, long long batch,
+                               long long size, PermArgs a) {
+  const long long total = batch * size;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long b = idx / size;
+    long long r = idx - b * size, src = 0;
+    for (int k = a.nd - 1; k >= 0; --k) {
+      const long long c = r % a.od[k];
+      r /= a.od[k];
+      src += c * a.is[k];
+    }
+    out[idx] = in[b * size + src];
+  }
+}
+
+template <class T>
+__global__ void pair_dot_kernel(const T* __restrict__ bra, long long bra_stride,
+                                const T* __restrict__ Z, long long z_stride, long long n,
+                                const int* __restrict__ pb, double* __restrict__ out) {
+  const int pair = blockIdx.x;
+  const T* a = bra + (long long)pb[pair] * bra_stride;
+  const T* z = Z + (long long)pair * z_stride;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) acc += (double)a[i] * (double)z[i];
+  __shared__ double red[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) out[pair] = acc;
+  }
+}
+
+template <class T>
+__global__ void shift_axpy_kernel(T* __restrict__ y, const T* __restrict__ x,
+                                  const double* __restrict__ shift, long long size,
+                                  long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i / size;
+    y[i] = y[i] - (T)shift[s] * x[i];
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out,
+                              long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+__global__ void to_f64_kernel(const float* __restrict__ in, double* __restrict__ out,
+                              long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+__global__ void scatter_gram_kernel(const double* __restrict__ g, int n_pairs,
+                                    const int* __restrict__ pb, const int* __restrict__ pk,
+                                    int symmetric, double* __restrict__ out, int ld) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
+  out[(long long)pb[i] * ld + pk[i]] = g[i];
+  if (symmetric) out[(long long)pk[i] * ld + pb[i]] = g[i];
+}
+
+int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+// Host-side proof that every address the launch can form lies inside its buffer: for each item
+// and segment, the smallest and largest offsets over (m, n, k) and over all pairs.
+static void check_bounds(const GemmDesc& g, size_t elem) {
+  auto base_max = [&](int mode, long long pstride) -> long long {
+    if (mode == MODE_PAIR) return (long long)(g.n_pairs - 1) * pstride;
+    if (mode == MODE_BRA) return (long long)g.max_bra * pstride;
+    if (mode == MODE_KET) return (long long)g.max_ket * pstride;
+    return 0;
+  };
+  TTN_REQUIRE(g.hst && (int)g.hst->sub_c.size() == g.st.n_sub, "gemm: missing host tables");
+  const long long a_hi = base_max(g.A.mode, g.A.pstride) + (long long)(g.M - 1) * g.a_sm +
+                         (long long)(g.K - 1) * g.a_sk;
+  const long long b_hi = base_max(g.B.mode, g.B.pstride) + (long long)(g.N - 1) * g.b_sn +
+                         (long long)(g.K - 1) * g.b_sk;
+  const long long c_hi = base_max(g.c_mode, g.c_pstride) + (long long)(g.M - 1) * g.c_sm +
+                         (long long)(g.N - 1) * g.c_sn;
+  for (int s = 0; s < g.st.n_sub; ++s) {
+    const long long c0 = g.hst->sub_c[s];
+    if (c0 < 0 || c0 + c_hi >= g.c_len)
+      TTN_FAIL(TTN_EINVAL, "gemm bounds: C item %d reaches %lld of %lld (elem %zu)", s, c0 + c_hi,
+               g.c_len, elem);
+    if (g.K <= 0) continue;
+    for (int q = g.hst->seg_ptr[s]; q < g.hst->seg_ptr[s + 1]; ++q) {
+      const long long a0 = g.hst->seg_a[q], b0 = g.hst->seg_b[q];
+      if (a0 < 0 || a0 + a_hi >= g.a_len)
+        TTN_FAIL(TTN_EINVAL, "gemm bounds: A seg %d reaches %lld of %lld", q, a0 + a_hi,
+                 g.a_len);
+      if (b0 < 0 || b0 + b_hi >= g.b_len)
+        TTN_FAIL(TTN_EINVAL, "gemm bounds: B seg %d reaches %lld of %lld", q, b0 + b_hi,
+                 g.b_len);
+    }
+  }
+}
+
+template <class T>
+void launch_gemm(ttn_ctx* ctx, const GemmDesc& g) {
+  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  check_bounds(g, sizeof(T));
+  int best = 0;
+  long long best_cost = -1;
+  for (int c = 0; c < 6; ++c) {
+    const long long tm = (g.M + kCfgs[c].bm - 1) / kCfgs[c].bm;
+    const long long tn = (g.N + kCfgs[c].bn - 1) / kCfgs[c].bn;
+    const long long cost = tm * kCfgs[c].bm * tn * kCfgs[c].bn + tm * tn * 1024;
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  const int tm = (g.M + kCfgs[best].bm - 1) / kCfgs[best].bm;
+  const int tn = (g.N + kCfgs[best].bn - 1) / kCfgs[best].bn;
+  const long long grid = (long long)tm * tn * g.st.n_sub * g.n_pairs;
+  if (grid > 0x7fffffffLL) TTN_FAIL(TTN_EUNSUPPORTED, "gemm grid too large (%lld)", grid);
+  dispatch<T>(best, g, tm, tn, grid, ctx->stream);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+template <class T>
+void launch_permute(ttn_ctx* ctx, const T* in, T* out, long long batch, int nd, const int* dims,
+                    const int* perm) {
+  PermArgs a{};
+  a.nd = nd;
+  long long stride[8], size = 1;
+  for (int k = nd - 1; k >= 0; --k) {
+    stride[k] = size;
+    size *= dims[k];
+  }
+  for (int k = 0; k < nd; ++k) {
+    a.od[k] = dims[perm[k]];
+    a.is[k] = stride[perm[k]];
+  }
+  if (batch * size == 0) return;
+  permute_kernel<T><<<grid_for(batch * size), kThreads, 0, ctx->stream>>>(in, out, batch, size,
+                                                                          a);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+template <class T>
+void launch_pair_dot(ttn_ctx* ctx, const T* bra, long long bra_stride, const T* Z,
+                     long long z_stride, long long n, int n_pairs, const int* pair_bra,
+                     double* out, int max_bra, long long bra_len, long long z_len) {
+  if (n_pairs <= 0) return;
+  TTN_REQUIRE((long long)max_bra * bra_stride + n <= bra_len &&
+                  (long long)(n_pairs - 1) * z_stride + n <= z_len,
+              "pair_dot bounds: bra %lld/%lld, Z %lld/%lld", (long long)max_bra * bra_stride + n,
+              bra_len, (long long)(n_pairs - 1) * z_stride + n, z_len);
+  pair_dot_kernel<T><<<n_pairs, kThreads, 0, ctx->stream>>>(bra, bra_stride, Z, z_stride, n,
+                                                             pair_bra, out);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+template <class T>
+void launch_shift_axpy(ttn_ctx* ctx, T* y, const T* x, const double* shift, int n_states,
+                       long long size) {
+  const long long total = (long long)n_states * size;
+  if (total == 0) return;
+  shift_axpy_kernel<T><<<grid_for(total), kThreads, 0, ctx->stream>>>(y, x, shift, size, total);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+void launch_to_f32(ttn_ctx* ctx, const double* in, float* out, long long n) {
+  if (n == 0) return;
+  to_f32_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n) {
+  if (n == 0) return;
+  to_f64_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* pb,
+                         const int* pk, int symmetric, double* out, int ld) {
+  if (n_pairs <= 0) return;
+  scatter_gram_kernel<<<(n_pairs + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
+      g, n_pairs, pb, pk, symmetric, out, ld);
+  ctx->launches++;
+  CUDA_LAUNCH_CHECK();
+}
+
+template void launch_gemm<double>(ttn_ctx*, const GemmDesc&);
+template void launch_gemm<float>(ttn_ctx*, const GemmDesc&);
+template void launch_permute<double>(ttn_ctx*, const double*, double*, long long, int,
+                                     const int*, const int*);
+template void launch_permute<float>(ttn_ctx*, const float*, float*, long long, int, const int*,
+                                    const int*);
+template void launch_pair_dot<double>(ttn_ctx*, const double*, long long, const double*,
+                                      long long, long long, int, const int*, double*, int,
+                                      long long, long long);
+template void launch_pair_dot<float>(ttn_ctx*, const float*, long long, const float*, long long,
+                                     long long, int, const int*, double*, int, long long,
+                                     long long);
+template void launch_shift_axpy<double>(ttn_ctx*, double*, const double*, const double*, int,
+                                        long long);
+template void launch_shift_axpy<float>(ttn_ctx*, float*, const float*, const double*, int,
+                                       long long);
