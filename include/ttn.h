@@ -71,6 +71,17 @@ const char* ttn_last_error(const ttn_ctx* ctx);
 ttn_status ttn_synchronize(ttn_ctx* ctx);
 /* Number of kernels this context has launched so far (for launch accounting). */
 long long ttn_launch_count(const ttn_ctx* ctx);
+/* Algorithmic flops of every contraction GEMM launched so far: 2*M*N*K per item and segment
+ * of the block-sparse contraction (no padding, no zero TTNO blocks). */
+double ttn_flop_count(const ttn_ctx* ctx);
+/* Turn per-launch timing on (1) or off (0) and clear the records. While on, every launch is
+ * bracketed by CUDA events recorded on the context's stream. */
+ttn_status ttn_profile_enable(ttn_ctx* ctx, int on);
+/* Per-kernel totals since the last ttn_profile_enable: kernel name (64 chars each, NUL
+ * terminated), launches, summed event time in ms, algorithmic flops and bytes. Arrays hold
+ * max_kernels entries; *n_kernels receives the number of distinct kernels (may exceed it). */
+ttn_status ttn_profile_get(ttn_ctx* ctx, int max_kernels, char* names, long long* launches,
+                           double* ms, double* flops, double* bytes, int* n_kernels);
 
 /* ---- tree (Sec. II.A.2, Eq. ttns; Appendix B trees) -------------------------------------- */
 

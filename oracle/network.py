@@ -21,6 +21,11 @@ from dataclasses import dataclass
 
 import numpy as np
 
+# Contraction-path search for numpy.einsum: greedy pairwise order with intermediates allowed up
+# to 2^31 elements (the default cap of the largest input's size forces an unfactored loop over
+# every index, which is exact but intractable at the paper's sizes).
+_PATH = ("greedy", 1 << 31)
+
 # ----------------------------------------------------------------------------------------------
 # tree helpers
 # ----------------------------------------------------------------------------------------------
@@ -119,7 +124,7 @@ def ttns_to_dense(tree, tensors):
             sub.append(mode_ax[int(tree.mode[i])])
         args += [tensors[i], sub]
     out = [mode_ax[m] for m in sorted(mode_ax)]
-    return np.einsum(*args, out, optimize=True).reshape(-1)
+    return np.einsum(*args, out, optimize=_PATH).reshape(-1)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -272,7 +277,7 @@ def ttno_to_dense(tree, ttno):
             W = W[..., 0, 0]
         args += [W, sub]
     out = [pax[m] for m in sorted(pax)] + [qax[m] for m in sorted(qax)]
-    H = np.einsum(*args, out, optimize=True)
+    H = np.einsum(*args, out, optimize=_PATH)
     N = int(np.sqrt(H.size))
     return H.reshape(N, N)
 
@@ -308,7 +313,7 @@ def node_contract(tree, ttno, t, ket, envs, bra=None, open_leg=None):
         out = []
     else:
         out = a + [p]
-    r = np.einsum(*args, out, optimize=True)
+    r = np.einsum(*args, out, optimize=_PATH)
     if bra is None:
         r = r.reshape(ket.shape)
     return r
@@ -411,7 +416,7 @@ def overlap(tree, A, B):
         for m, c in enumerate(tree.children(t)):
             args += [E[c], [a[m + off], b[m + off]]]
         out = [a[0], b[0]] if off else []
-        E[t] = np.einsum(*args, out, optimize=True)
+        E[t] = np.einsum(*args, out, optimize=_PATH)
     return float(E[tree.root])
 
 

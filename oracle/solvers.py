@@ -13,7 +13,8 @@ Readings of points the paper leaves open (each is listed with its reason in the 
 * LOBPCG (Alg. 2): x_j <- sum_{k=1}^{3n} v_kj s_k then normalised, p_j <- sum_{k>n} v_kj s_k,
   iteration 1 uses S = {x} u {r}; the Gram pencil is solved by canonical orthogonalisation
   (drop eigenvalues of M below eps * max);
-* fitting starts from the input state with the largest |coefficient| (first one on ties).
+* fitting starts from the input state with the largest |coefficient| (first one on ties);
+* Ritz vectors carry a fixed sign: their largest-magnitude entry is positive.
 """
 from __future__ import annotations
 
@@ -192,7 +193,18 @@ def rayleigh_ritz(Ht, Mt, n, eps=1e-12):
     X = U[:, keep] / np.sqrt(mu[keep])
     theta, Y = np.linalg.eigh(X.T @ Ht @ X)
     V = X @ Y
-    return theta[:n], V[:, :n]
+    return theta[:n], _sign_fixed(V[:, :n])
+
+
+def _sign_fixed(V):
+    """Eigenvectors are defined up to sign; fix it so that the entry of largest magnitude
+    (first one on ties) of each column is positive."""
+    V = V.copy()
+    for j in range(V.shape[1]):
+        k = int(np.argmax(np.abs(V[:, j])))
+        if V[k, j] < 0:
+            V[:, j] = -V[:, j]
+    return V
 
 
 def gram_block(tree, ttno, states):

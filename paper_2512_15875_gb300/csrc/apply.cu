@@ -113,10 +113,11 @@ extern "C" ttn_status ttn_apply_block(ttn_ctx* ctx, const ttn_ttno* Hc, const tt
         DevBuf dop(gop.size() * sizeof(double), s);
         CUDA_CHECK(cudaMemcpyAsync(dop.p, gop.data(), gop.size() * sizeof(double),
                                    cudaMemcpyHostToDevice, s));
+        LaunchScope ls(ctx, "apply_f64", 2.0 * total * d,
+                       8.0 * ((double)in->n_states * a.in_size + total));
         apply_kernel<double><<<blocks, 256, 0, s>>>(in->node64(t), ob->node64(t),
                                                     doff.as<long long>(), dop.as<double>(), ng,
                                                     in->n_states, a);
-        ctx->launches++;
         CUDA_LAUNCH_CHECK();
         CUDA_CHECK(cudaStreamSynchronize(s));
       } else {
@@ -124,10 +125,11 @@ extern "C" ttn_status ttn_apply_block(ttn_ctx* ctx, const ttn_ttno* Hc, const tt
         DevBuf dop(g32.size() * sizeof(float), s);
         CUDA_CHECK(cudaMemcpyAsync(dop.p, g32.data(), g32.size() * sizeof(float),
                                    cudaMemcpyHostToDevice, s));
+        LaunchScope ls(ctx, "apply_f32", 2.0 * total * d,
+                       4.0 * (double)in->n_states * a.in_size + 8.0 * total);
         apply_kernel<float><<<blocks, 256, 0, s>>>(in->node32(t), ob->node64(t),
                                                    doff.as<long long>(), dop.as<float>(), ng,
                                                    in->n_states, a);
-        ctx->launches++;
         CUDA_LAUNCH_CHECK();
         CUDA_CHECK(cudaStreamSynchronize(s));
       }

@@ -76,6 +76,14 @@ NodePlan& get_plan(ttn_ttno* H, int t, int open) {
   p.d_ocomb64 = DevBuf(no * sizeof(double), st);
   p.d_ocomb32 = DevBuf(no * sizeof(float), st);
   std::vector<float> o32(p.ocomb.begin(), p.ocomb.end());
+  p.d_slot_ptr = DevBuf(p.slot_ptr.size() * sizeof(int), st);
+  p.d_grp_prefix = DevBuf(std::max<size_t>(p.grp_prefix.size(), 1) * sizeof(int), st);
+  CUDA_CHECK(cudaMemcpyAsync(p.d_slot_ptr.p, p.slot_ptr.data(), p.slot_ptr.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st));
+  if (!p.grp_prefix.empty())
+    CUDA_CHECK(cudaMemcpyAsync(p.d_grp_prefix.p, p.grp_prefix.data(),
+                               p.grp_prefix.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
   if (!p.ocomb.empty()) {
     CUDA_CHECK(cudaMemcpyAsync(p.d_ocomb64.p, p.ocomb.data(), p.ocomb.size() * sizeof(double),
                                cudaMemcpyHostToDevice, st));
@@ -196,8 +204,11 @@ const float* block_node<float>(const ttn_block* b, int t) {
 template <class T>
 void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
              const ttn_block* ket, const PairSet& ps, const std::vector<const T*>& env,
-             const std::vector<int>& env_da, void* out, long long out_len, int out_kind) {
+             const std::vector<int>& env_da, void* out, long long out_len, int out_kind,
+             const T* ket_ptr, int ket_n) {
   const int P = ps.P;
+  const T* ket_data = ket_ptr ? ket_ptr : block_node<T>(ket, t);
+  const int n_ket = ket_ptr ? ket_n : ket->n_states;
   const int* d_pb = ps.d_pb;
   const int* d_pk = ps.d_pk;
   const TreeInfo& tr = H->tree;
@@ -221,12 +232,11 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
   perm.push_back(nl);
   if (open >= 0) perm.push_back(open);
   const long long ksize = ket->size[t];
-  DevBuf kp((size_t)ket->n_states * ksize * sizeof(T), st);
-  launch_permute<T>(ctx, block_node<T>(ket, t), kp.as<T>(), ket->n_states, nl + 1, kd.data(),
-                    perm.data());
+  DevBuf kp((size_t)n_ket * ksize * sizeof(T), st);
+  launch_permute<T>(ctx, ket_data, kp.as<T>(), n_ket, nl + 1, kd.data(), perm.data());
 
   const void* prev = kp.p;
-  long long prev_len = (long long)ket->n_states * ksize;
+  long long prev_len = (long long)n_ket * ksize;
   int prev_mode = MODE_KET;
   long long prev_pstride = ksize;
   std::vector<DevBuf> Tl(mC + 1);
@@ -255,7 +265,7 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.pair_ket = d_pk;
     g.st = tab.stages[l - 1];
     g.hst = &tab.host[l - 1];
-    g.a_len = l == 1 ? (long long)ket->n_states * ksize : prev_len;
+    g.a_len = l == 1 ? (long long)n_ket * ksize : prev_len;
     g.b_len = (long long)P * Dw[c] * Da[c] * Db[c];
     g.c_len = (long long)P * g.c_pstride;
     g.max_bra = ps.max_bra;
@@ -276,33 +286,27 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     Z = zbuf.p;
   }
   {
-    GemmDesc g{};
-    g.M = (int)zrest;
-    g.N = d;
-    g.K = d;
-    g.a_sm = 1;
-    g.a_sk = zrest;
-    g.b_sn = d;
-    g.b_sk = 1;
-    g.c_sm = d;
-    g.c_sn = 1;
-    g.A = {prev, prev_mode, prev_pstride};
-    const void* oc = sizeof(T) == 8 ? p.d_ocomb64.p : p.d_ocomb32.p;
-    g.B = {oc, MODE_CONST, 0};
-    g.C = Z;
-    g.c_mode = MODE_PAIR;
-    g.c_pstride = (long long)p.n_slots * zsize;
-    g.n_pairs = P;
-    g.pair_bra = d_pb;
-    g.pair_ket = d_pk;
-    g.st = tab.stages[mC];
-    g.hst = &tab.host[mC];
-    g.a_len = prev_len;
-    g.b_len = std::max<long long>((long long)p.ocomb.size(), 1);
-    g.c_len = out_kind == OUT_LOCAL ? out_len : (long long)P * g.c_pstride;
-    g.max_bra = ps.max_bra;
-    g.max_ket = ps.max_ket;
-    launch_gemm<T>(ctx, g);
+    OpStageDesc o{};
+    o.d = d;
+    o.rows = (int)zrest;
+    o.n_slots = p.n_slots;
+    o.n_groups = (int)p.grp_prefix.size();
+    o.tsize = zsize;
+    o.A = {prev, prev_mode, prev_pstride};
+    o.slot_ptr = p.d_slot_ptr.as<int>();
+    o.grp_prefix = p.d_grp_prefix.as<int>();
+    o.ops = sizeof(T) == 8 ? p.d_ocomb64.p : p.d_ocomb32.p;
+    o.Z = Z;
+    o.z_pstride = (long long)p.n_slots * zsize;
+    o.n_pairs = P;
+    o.pair_bra = d_pb;
+    o.pair_ket = d_pk;
+    o.a_len = prev_len;
+    o.z_len = out_kind == OUT_LOCAL ? out_len : (long long)P * o.z_pstride;
+    o.max_ket = ps.max_ket;
+    o.max_prefix = 0;
+    for (int x : p.grp_prefix) o.max_prefix = std::max(o.max_prefix, x);
+    launch_op_stage<T>(ctx, o);
   }
 
   if (out_kind == OUT_ENV) {
@@ -389,10 +393,11 @@ void envs_compute(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_blo
 
 template void node_op<double>(ttn_ctx*, ttn_ttno*, int, int, const ttn_block*, const ttn_block*,
                               const PairSet&, const std::vector<const double*>&,
-                              const std::vector<int>&, void*, long long, int);
+                              const std::vector<int>&, void*, long long, int, const double*,
+                              int);
 template void node_op<float>(ttn_ctx*, ttn_ttno*, int, int, const ttn_block*, const ttn_block*,
                              const PairSet&, const std::vector<const float*>&,
-                             const std::vector<int>&, void*, long long, int);
+                             const std::vector<int>&, void*, long long, int, const float*, int);
 template void envs_compute<double>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
                                    const PairSet&, int, std::vector<DevBuf>&,
                                    std::vector<DevBuf>&);

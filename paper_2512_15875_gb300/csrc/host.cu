@@ -568,6 +568,11 @@ void ttn_destroy(ttn_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   g_id_cache.erase(ctx);
   cudaStreamSynchronize(ctx->stream);
+  for (auto& r : ctx->prof) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -580,6 +585,51 @@ ttn_status ttn_synchronize(ttn_ctx* ctx) {
 }
 
 long long ttn_launch_count(const ttn_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+double ttn_flop_count(const ttn_ctx* ctx) { return ctx ? ctx->flops_total : 0.0; }
+
+ttn_status ttn_profile_enable(ttn_ctx* ctx, int on) {
+  if (!ctx) return TTN_EINVAL;
+  return guarded(ctx, [&] {
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    for (auto& r : ctx->prof) {
+      ctx->event_pool.push_back(r.start);
+      ctx->event_pool.push_back(r.stop);
+    }
+    ctx->prof.clear();
+    ctx->profiling = on != 0;
+  });
+}
+
+ttn_status ttn_profile_get(ttn_ctx* ctx, int max_kernels, char* names, long long* launches,
+                           double* ms, double* flops, double* bytes, int* n_kernels) {
+  if (!ctx || !n_kernels) return TTN_EINVAL;
+  return guarded(ctx, [&] {
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+    const int nk = (int)ctx->prof_names.size();
+    std::vector<long long> cnt(nk, 0);
+    std::vector<double> t(nk, 0.0), f(nk, 0.0), b(nk, 0.0);
+    for (auto& r : ctx->prof) {
+      float e = 0.f;
+      CUDA_CHECK(cudaEventElapsedTime(&e, r.start, r.stop));
+      cnt[r.name]++;
+      t[r.name] += e;
+      f[r.name] += r.flops;
+      b[r.name] += r.bytes;
+    }
+    *n_kernels = nk;
+    for (int i = 0; i < nk && i < max_kernels; ++i) {
+      if (names) {
+        std::strncpy(names + 64 * i, ctx->prof_names[i].c_str(), 63);
+        names[64 * i + 63] = 0;
+      }
+      if (launches) launches[i] = cnt[i];
+      if (ms) ms[i] = t[i];
+      if (flops) flops[i] = f[i];
+      if (bytes) bytes[i] = b[i];
+    }
+  });
+}
 
 // ------------------------------------------------------------------------------------------------
 // tree / TTNO
@@ -923,9 +973,10 @@ static long long gram_bytes_per_pair(ttn_ttno* H, const ttn_block* bra, const tt
   return (envb + inter) * (long long)sizeof(T) + 64;
 }
 
+// <bra_pb[i]| H |ket_pk[i]> for every listed pair, written to d_out[i] (device, float64).
 template <class T>
-static void gram_run(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
-                     const std::vector<int>& pb, const std::vector<int>& pk, double* d_out) {
+void gram_pairs(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                const std::vector<int>& pb, const std::vector<int>& pk, double* d_out) {
   const int n_pairs = (int)pb.size();
   if (n_pairs == 0) return;
   const long long per = gram_bytes_per_pair<T>(H, bra, ket);
@@ -949,6 +1000,11 @@ static void gram_run(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_
   }
 }
 
+template void gram_pairs<double>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
+                                 const std::vector<int>&, const std::vector<int>&, double*);
+template void gram_pairs<float>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
+                                const std::vector<int>&, const std::vector<int>&, double*);
+
 void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
                  double* d_mat, int ld, int prec) {
   const bool sym = bra == ket;
@@ -959,8 +1015,8 @@ void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_bloc
       pk.push_back(l);
     }
   DevBuf g(std::max<size_t>(pb.size(), 1) * sizeof(double), ctx->stream);
-  if (prec == TTN_FP64) gram_run<double>(ctx, H, bra, ket, pb, pk, g.as<double>());
-  else gram_run<float>(ctx, H, bra, ket, pb, pk, g.as<double>());
+  if (prec == TTN_FP64) gram_pairs<double>(ctx, H, bra, ket, pb, pk, g.as<double>());
+  else gram_pairs<float>(ctx, H, bra, ket, pb, pk, g.as<double>());
   DevInts dpb(pb, ctx->stream), dpk(pk, ctx->stream);
   launch_scatter_gram(ctx, g.as<double>(), (int)pb.size(), dpb.get(), dpk.get(), sym ? 1 : 0,
                       d_mat, ld);

@@ -81,12 +81,32 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Launch statistics: when profiling is on, each launch is bracketed by CUDA events on the
+// context stream and attributed to a kernel name with its algorithmic flops and bytes.
+struct LaunchRecord {
+  int name;
+  cudaEvent_t start, stop;
+  double flops, bytes;
+};
 struct ttn_ctx {
   int device = 0;
   cudaStream_t stream = 0;
   bool own_stream = false;
   std::string last_error;
   long long launches = 0;
+  bool profiling = false;
+  std::vector<std::string> prof_names;
+  std::vector<LaunchRecord> prof;
+  std::vector<cudaEvent_t> event_pool;
+  double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
+};
+
+// RAII helper: records the launch's events (if profiling) and counts it.
+struct LaunchScope {
+  ttn_ctx* ctx;
+  int idx = -1;
+  LaunchScope(ttn_ctx* c, const char* name, double flops, double bytes);
+  ~LaunchScope();
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -102,6 +122,7 @@ struct TtnoEntry {
 // the contracted legs and the per-output-slot groups with their combined local operators.
 struct NodePlan {
   int node = -1, open = -1;
+  DevBuf d_slot_ptr, d_grp_prefix;                     // device copies for the operator stage
   std::vector<int> C;                                  // contracted legs in order
   std::vector<std::vector<std::pair<int, int>>> level; // level[l]: (parent prefix, w) per prefix
   int n_slots = 1;
@@ -222,6 +243,26 @@ struct PairSet {
 };
 
 template <class T> void launch_gemm(ttn_ctx* ctx, const GemmDesc& g);
+
+// Operator stage of a node contraction (see engine.cu):
+//   Z[pair][slot][r][p] = sum_{g in slot} sum_q Tm[pair][prefix_g][q][r] * O_g[p][q]
+struct OpStageDesc {
+  int d, rows, n_slots, n_groups;
+  long long tsize;          // d * rows: one prefix slice of Tm
+  GemmOperand A;            // Tm base (pair- or ket-indexed)
+  const int* slot_ptr;      // [n_slots + 1]
+  const int* grp_prefix;    // [n_groups]
+  const void* ops;          // [n_groups][d][d]
+  void* Z;
+  long long z_pstride;      // n_slots * d * rows
+  int n_pairs;
+  const int* pair_bra;
+  const int* pair_ket;
+  // host-side validation
+  long long a_len, z_len;
+  int max_ket, max_prefix;
+};
+template <class T> void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o);
 template <class T>
 void launch_permute(ttn_ctx* ctx, const T* in, T* out, long long batch, int nd, const int* dims,
                     const int* perm);
@@ -242,10 +283,14 @@ void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* 
 // ------------------------------------------------------------------------------------------------
 enum { OUT_ENV = 0, OUT_SCALAR = 1, OUT_LOCAL = 2 };
 
+// Contract node t (see engine.cu). `ket` supplies the ket bond dimensions and, unless
+// ket_ptr is given, the ket tensors; ket_ptr (ket_n states of the node's size, contiguous)
+// replaces them, e.g. with Krylov vectors.
 template <class T>
 void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
              const ttn_block* ket, const PairSet& ps, const std::vector<const T*>& env,
-             const std::vector<int>& env_da, void* out, long long out_len, int out_kind);
+             const std::vector<int>& env_da, void* out, long long out_len, int out_kind,
+             const T* ket_ptr = nullptr, int ket_n = 0);
 
 template <class T>
 void envs_compute(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,

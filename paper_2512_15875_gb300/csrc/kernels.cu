@@ -243,10 +243,44 @@ static void check_bounds(const GemmDesc& g, size_t elem) {
   }
 }
 
+static cudaEvent_t pool_event(ttn_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  CUDA_CHECK(cudaEventCreate(&e));
+  return e;
+}
+
+LaunchScope::LaunchScope(ttn_ctx* c, const char* name, double flops, double bytes) : ctx(c) {
+  ctx->launches++;
+  ctx->flops_total += flops;
+  if (!ctx->profiling) return;
+  int id = -1;
+  for (size_t i = 0; i < ctx->prof_names.size(); ++i)
+    if (ctx->prof_names[i] == name) id = (int)i;
+  if (id < 0) {
+    id = (int)ctx->prof_names.size();
+    ctx->prof_names.push_back(name);
+  }
+  LaunchRecord r{id, pool_event(ctx), pool_event(ctx), flops, bytes};
+  CUDA_CHECK(cudaEventRecord(r.start, ctx->stream));
+  idx = (int)ctx->prof.size();
+  ctx->prof.push_back(r);
+}
+
+LaunchScope::~LaunchScope() {
+  if (idx >= 0) cudaEventRecord(ctx->prof[idx].stop, ctx->stream);
+}
+
 template <class T>
 void launch_gemm(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
   check_bounds(g, sizeof(T));
+  long long nseg = 0;
+  for (int s = 0; s < g.st.n_sub; ++s) nseg += g.hst->seg_ptr[s + 1] - g.hst->seg_ptr[s];
   int best = 0;
   long long best_cost = -1;
   for (int c = 0; c < 6; ++c) {
@@ -262,8 +296,15 @@ void launch_gemm(ttn_ctx* ctx, const GemmDesc& g) {
   const int tn = (g.N + kCfgs[best].bn - 1) / kCfgs[best].bn;
   const long long grid = (long long)tm * tn * g.st.n_sub * g.n_pairs;
   if (grid > 0x7fffffffLL) TTN_FAIL(TTN_EUNSUPPORTED, "gemm grid too large (%lld)", grid);
+  static const char* names64[] = {"gemm_f64_64x64", "gemm_f64_64x32", "gemm_f64_32x32",
+                                  "gemm_f64_128x16", "gemm_f64_64x16", "gemm_f64_16x16"};
+  static const char* names32[] = {"gemm_f32_64x64", "gemm_f32_64x32", "gemm_f32_32x32",
+                                  "gemm_f32_128x16", "gemm_f32_64x16", "gemm_f32_16x16"};
+  const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
+  const double bytes = (double)sizeof(T) * g.n_pairs *
+                       ((double)g.M * g.N * g.st.n_sub + (double)(g.M + g.N) * g.K * nseg);
+  LaunchScope ls(ctx, sizeof(T) == 8 ? names64[best] : names32[best], flops, bytes);
   dispatch<T>(best, g, tm, tn, grid, ctx->stream);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
@@ -282,9 +323,9 @@ void launch_permute(ttn_ctx* ctx, const T* in, T* out, long long batch, int nd, 
     a.is[k] = stride[perm[k]];
   }
   if (batch * size == 0) return;
+  LaunchScope ls(ctx, "permute", 0.0, 2.0 * sizeof(T) * batch * size);
   permute_kernel<T><<<grid_for(batch * size), kThreads, 0, ctx->stream>>>(in, out, batch, size,
                                                                           a);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
@@ -297,9 +338,9 @@ void launch_pair_dot(ttn_ctx* ctx, const T* bra, long long bra_stride, const T* 
                   (long long)(n_pairs - 1) * z_stride + n <= z_len,
               "pair_dot bounds: bra %lld/%lld, Z %lld/%lld", (long long)max_bra * bra_stride + n,
               bra_len, (long long)(n_pairs - 1) * z_stride + n, z_len);
+  LaunchScope ls(ctx, "pair_dot", 2.0 * n * n_pairs, 2.0 * sizeof(T) * n * n_pairs);
   pair_dot_kernel<T><<<n_pairs, kThreads, 0, ctx->stream>>>(bra, bra_stride, Z, z_stride, n,
                                                              pair_bra, out);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
@@ -308,33 +349,136 @@ void launch_shift_axpy(ttn_ctx* ctx, T* y, const T* x, const double* shift, int 
                        long long size) {
   const long long total = (long long)n_states * size;
   if (total == 0) return;
+  LaunchScope ls(ctx, "shift_axpy", 2.0 * total, 3.0 * sizeof(T) * total);
   shift_axpy_kernel<T><<<grid_for(total), kThreads, 0, ctx->stream>>>(y, x, shift, size, total);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
 void launch_to_f32(ttn_ctx* ctx, const double* in, float* out, long long n) {
   if (n == 0) return;
+  LaunchScope ls(ctx, "to_f32", 0.0, 12.0 * n);
   to_f32_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
 void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n) {
   if (n == 0) return;
+  LaunchScope ls(ctx, "to_f64", 0.0, 12.0 * n);
   to_f64_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
 
 void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* pb,
                          const int* pk, int symmetric, double* out, int ld) {
   if (n_pairs <= 0) return;
+  LaunchScope ls(ctx, "scatter_gram", 0.0, 24.0 * n_pairs);
   scatter_gram_kernel<<<(n_pairs + kThreads - 1) / kThreads, kThreads, 0, ctx->stream>>>(
       g, n_pairs, pb, pk, symmetric, out, ld);
-  ctx->launches++;
   CUDA_LAUNCH_CHECK();
 }
+
+// One thread per output row r of one (pair, slot); all d outputs of the row in registers.
+// The combined operators of the slot's groups are staged through shared memory in chunks;
+// the output tile is transposed through shared memory so the global stores are coalesced.
+template <class T, int D>
+__global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int rtiles) {
+  extern __shared__ unsigned char sh_raw[];
+  T* sh = reinterpret_cast<T*>(sh_raw);
+  constexpr int kOpElems = 8192 / sizeof(T) * 4;   // 32 KB of operators per chunk
+  constexpr int GCH = kOpElems / (D * D) > 0 ? kOpElems / (D * D) : 1;
+  T* sop = sh;
+  T* sout = sh + GCH * D * D;                        // kThreads x (D + 1)
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int slot = (int)(rest % o.n_slots);
+  const int pair = (int)(rest / o.n_slots);
+  long long aidx = 0;
+  if (o.A.mode == MODE_PAIR) aidx = pair;
+  else if (o.A.mode == MODE_KET) aidx = o.pair_ket[pair];
+  else if (o.A.mode == MODE_BRA) aidx = o.pair_bra[pair];
+  const T* Tb = static_cast<const T*>(o.A.base) + aidx * o.A.pstride;
+  const T* ops = static_cast<const T*>(o.ops);
+  const int r0 = rt * kThreads;
+  const int r = r0 + threadIdx.x;
+  T acc[D];
+#pragma unroll
+  for (int p = 0; p < D; ++p) acc[p] = T(0);
+  const int g0 = o.slot_ptr[slot], g1 = o.slot_ptr[slot + 1];
+  for (int gc = g0; gc < g1; gc += GCH) {
+    const int ng = min(GCH, g1 - gc);
+    for (int i = threadIdx.x; i < ng * D * D; i += kThreads)
+      sop[i] = ops[(long long)gc * D * D + i];
+    __syncthreads();
+    if (r < o.rows) {
+      for (int g = 0; g < ng; ++g) {
+        const T* src = Tb + (long long)o.grp_prefix[gc + g] * o.tsize + r;
+        const T* O = sop + g * D * D;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          const T t = src[(long long)q * o.rows];
+#pragma unroll
+          for (int p = 0; p < D; ++p) acc[p] = fma(O[p * D + q], t, acc[p]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < D; ++p) sout[threadIdx.x * (D + 1) + p] = acc[p];
+  __syncthreads();
+  T* Zb = static_cast<T*>(o.Z) + (long long)pair * o.z_pstride +
+          (long long)slot * o.rows * D + (long long)r0 * D;
+  const int nrow = min(kThreads, o.rows - r0);
+  for (int i = threadIdx.x; i < nrow * D; i += kThreads)
+    Zb[i] = sout[(i / D) * (D + 1) + (i % D)];
+}
+
+template <class T, int D>
+static void op_stage_dispatch(ttn_ctx* ctx, const OpStageDesc& o, int rtiles, long long grid) {
+  constexpr int kOpElems = 8192 / sizeof(T) * 4;
+  constexpr int GCH = kOpElems / (D * D) > 0 ? kOpElems / (D * D) : 1;
+  const size_t shmem = sizeof(T) * ((size_t)GCH * D * D + (size_t)kThreads * (D + 1));
+  if (shmem > 48 * 1024)
+    CUDA_CHECK(cudaFuncSetAttribute(op_stage_kernel<T, D>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+  op_stage_kernel<T, D><<<grid, kThreads, shmem, ctx->stream>>>(o, rtiles);
+}
+
+template <class T>
+void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
+  if (o.n_pairs <= 0 || o.n_slots <= 0 || o.rows <= 0) return;
+  TTN_REQUIRE(o.d >= 1 && o.d <= 32, "operator stage: d = %d unsupported", o.d);
+  long long base_max = 0;
+  if (o.A.mode == MODE_PAIR) base_max = (long long)(o.n_pairs - 1) * o.A.pstride;
+  else if (o.A.mode == MODE_KET) base_max = (long long)o.max_ket * o.A.pstride;
+  TTN_REQUIRE(o.n_groups == 0 || base_max + (long long)(o.max_prefix + 1) * o.tsize <= o.a_len,
+              "op stage bounds: A reaches %lld of %lld",
+              base_max + (long long)(o.max_prefix + 1) * o.tsize, o.a_len);
+  TTN_REQUIRE((long long)o.n_pairs * o.z_pstride <= o.z_len &&
+                  (long long)o.n_slots * o.rows * o.d <= o.z_pstride,
+              "op stage bounds: Z");
+  const int rtiles = (o.rows + kThreads - 1) / kThreads;
+  const long long grid = (long long)rtiles * o.n_slots * o.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "op stage grid too large");
+  const double flops = 2.0 * o.d * o.d * (double)o.rows * o.n_groups * o.n_pairs;
+  const double bytes = (double)sizeof(T) * o.n_pairs *
+                       ((double)o.n_groups * o.tsize + (double)o.n_slots * o.rows * o.d);
+  LaunchScope ls(ctx, sizeof(T) == 8 ? "op_stage_f64" : "op_stage_f32", flops, bytes);
+  switch (o.d) {
+#define TTN_OPD(k) case k: op_stage_dispatch<T, k>(ctx, o, rtiles, grid); break;
+    TTN_OPD(1) TTN_OPD(2) TTN_OPD(3) TTN_OPD(4) TTN_OPD(5) TTN_OPD(6) TTN_OPD(7) TTN_OPD(8)
+    TTN_OPD(9) TTN_OPD(10) TTN_OPD(11) TTN_OPD(12) TTN_OPD(13) TTN_OPD(14) TTN_OPD(15)
+    TTN_OPD(16) TTN_OPD(17) TTN_OPD(18) TTN_OPD(19) TTN_OPD(20) TTN_OPD(21) TTN_OPD(22)
+    TTN_OPD(23) TTN_OPD(24) TTN_OPD(25) TTN_OPD(26) TTN_OPD(27) TTN_OPD(28) TTN_OPD(29)
+    TTN_OPD(30) TTN_OPD(31) TTN_OPD(32)
+#undef TTN_OPD
+  }
+  CUDA_LAUNCH_CHECK();
+}
+
+template void launch_op_stage<double>(ttn_ctx*, const OpStageDesc&);
+template void launch_op_stage<float>(ttn_ctx*, const OpStageDesc&);
 
 template void launch_gemm<double>(ttn_ctx*, const GemmDesc&);
 template void launch_gemm<float>(ttn_ctx*, const GemmDesc&);

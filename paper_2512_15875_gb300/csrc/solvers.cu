@@ -1,28 +1,1283 @@
-// Solver drivers (fitting, ALS, Rayleigh-Ritz, LOBPCG): placeholders until implemented.
+// Solver drivers on the GPU (Sec. II.B-C): QR gauge moves of the orthogonality centre, an
+// on-demand environment cache, batched MINRES (Paige & Saunders 1975) with device-side Lanczos
+// and Givens scalars, ALS and variational-fitting sweeps, Rayleigh-Ritz in float64 (cyclic
+// Jacobi), and block LOBPCG (Alg. 2).
+//
+// Readings of points the paper leaves open (same as the oracle): the solution TTNS is kept in
+// canonical form with the centre at the node being updated (R with a non-negative diagonal);
+// sweeps visit the nodes in depth-first pre-order from the root; MINRES warm-starts from the
+// current node tensor; fitting starts from the input state of the largest |coefficient|;
+// LOBPCG updates x_j = sum_{k<=3n} v_kj s_k (normalised), p_j = sum_{k>n} v_kj s_k and uses
+// S = {x} u {r} in its first iteration.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
 #include "internal.h"
 
+ttn_ttno* identity_for(ttn_ctx* ctx, const TreeInfo& tree);
+template <class T>
+void gram_pairs(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                const std::vector<int>& pb, const std::vector<int>& pk, double* d_out);
+void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                 double* d_mat, int ld, int prec);
+
+namespace {
+
+constexpr int kT = 256;
+
+int grid_of(long long n) {
+  long long b = (n + kT - 1) / kT;
+  return (int)std::max<long long>(1, std::min<long long>(b, 152 * 32));
+}
+
+// ----------------------------------------------------------------------------------------------
+// kernels
+// ----------------------------------------------------------------------------------------------
+
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Householder QR of one rows x D matrix per CTA (row-major, rows >= D): A is overwritten by the
+// reflectors, Q (rows x D) and R (D x D, non-negative diagonal) are written out.
+template <class T>
+__global__ void __launch_bounds__(kT) householder_qr_kernel(T* __restrict__ A, T* __restrict__ Q,
+                                                           T* __restrict__ R, int rows, int D,
+                                                           long long mstride) {
+  A += (long long)blockIdx.x * mstride;
+  Q += (long long)blockIdx.x * mstride;
+  R += (long long)blockIdx.x * D * D;
+  __shared__ T red[33];
+  __shared__ T tau[64];
+  __shared__ T wk[8][32];
+  __shared__ T par[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j < D; ++j) {
+    T part = 0;
+    for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) {
+      const T x = A[(long long)i * D + j];
+      part += x * x;
+    }
+    const T sigma = block_sum(part, red);
+    if (threadIdx.x == 0) {
+      const T alpha = A[(long long)j * D + j];
+      if (sigma == T(0)) {
+        tau[j] = 0;
+        par[0] = 0;
+      } else {
+        const T normx = sqrt(alpha * alpha + sigma);
+        const T beta = alpha <= T(0) ? normx : -normx;
+        tau[j] = (beta - alpha) / beta;
+        par[0] = T(1) / (alpha - beta);
+        A[(long long)j * D + j] = beta;
+      }
+    }
+    __syncthreads();
+    const T tj = tau[j];
+    if (tj != T(0)) {
+      const T sc = par[0];
+      for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) A[(long long)i * D + j] *= sc;
+      __syncthreads();
+      for (int k0 = j + 1; k0 < D; k0 += 32) {
+        const int k = k0 + lane;
+        T acc = 0;
+        if (k < D)
+          for (int i = j + warp; i < rows; i += 8) {
+            const T v = i == j ? T(1) : A[(long long)i * D + j];
+            acc += v * A[(long long)i * D + k];
+          }
+        wk[warp][lane] = acc;
+        __syncthreads();
+        T w = 0;
+        for (int q = 0; q < 8; ++q) w += wk[q][lane];
+        __syncthreads();
+        if (k < D)
+          for (int i = j + warp; i < rows; i += 8) {
+            const T v = i == j ? T(1) : A[(long long)i * D + j];
+            A[(long long)i * D + k] -= tj * v * w;
+          }
+        __syncthreads();
+      }
+    }
+  }
+  for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+    const int a = idx / D, b = idx % D;
+    R[idx] = b >= a ? A[(long long)a * D + b] : T(0);
+  }
+  for (long long idx = threadIdx.x; idx < (long long)rows * D; idx += blockDim.x) {
+    const long long i = idx / D;
+    const int k = (int)(idx % D);
+    Q[idx] = i == k ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = D - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj == T(0)) continue;
+    for (int k0 = j; k0 < D; k0 += 32) {
+      const int k = k0 + lane;
+      T acc = 0;
+      if (k < D)
+        for (int i = j + warp; i < rows; i += 8) {
+          const T v = i == j ? T(1) : A[(long long)i * D + j];
+          acc += v * Q[(long long)i * D + k];
+        }
+      wk[warp][lane] = acc;
+      __syncthreads();
+      T w = 0;
+      for (int q = 0; q < 8; ++q) w += wk[q][lane];
+      __syncthreads();
+      if (k < D)
+        for (int i = j + warp; i < rows; i += 8) {
+          const T v = i == j ? T(1) : A[(long long)i * D + j];
+          Q[(long long)i * D + k] -= tj * v * w;
+        }
+      __syncthreads();
+    }
+  }
+  // sign convention: diag(R) >= 0
+  for (int j = 0; j < D; ++j) {
+    if (R[j * D + j] < T(0)) {
+      __syncthreads();
+      for (int b = j + threadIdx.x; b < D; b += blockDim.x) R[j * D + b] = -R[j * D + b];
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) Q[(long long)i * D + j] =
+          -Q[(long long)i * D + j];
+    }
+    __syncthreads();
+  }
+}
+
+// out[s][o][k][i] = sum_b R[s][k][b] in[s][o][b][i]
+template <class T>
+__global__ void leg_product_kernel(const T* __restrict__ R, const T* __restrict__ in,
+                                   T* __restrict__ out, int n, long long size, long long inner,
+                                   int D) {
+  const long long total = (long long)n * size;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long s = idx / size;
+    const long long r = idx - s * size;
+    const long long i = r % inner;
+    const long long k = (r / inner) % D;
+    const long long o = r / (inner * D);
+    const T* Rk = R + (s * D + k) * D;
+    const T* src = in + s * size + o * D * inner + i;
+    T acc = 0;
+    for (int b = 0; b < D; ++b) acc += Rk[b] * src[(long long)b * inner];
+    out[idx] = acc;
+  }
+}
+
+// out[s] = sum_i x[s][i] * y[s][i] in float64, one CTA per state
+template <class T>
+__global__ void dot_kernel(const T* __restrict__ x, const T* __restrict__ y, long long n,
+                           double* __restrict__ out) {
+  __shared__ double red[33];
+  const long long off = (long long)blockIdx.x * n;
+  double acc = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x)
+    acc += (double)x[off + i] * (double)y[off + i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+template <class T>
+__global__ void scale_kernel(T* __restrict__ x, const double* __restrict__ f, long long n,
+                             int mode, int n_states) {
+  // mode 0: x *= f[s]; mode 1: x *= 1/sqrt(f[s]) (f > 0)
+  const long long total = (long long)n * n_states;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double g = f[idx / n];
+    const double sc = mode == 0 ? g : (g > 0.0 ? 1.0 / sqrt(g) : 0.0);
+    x[idx] = (T)((double)x[idx] * sc);
+  }
+}
+
+// out[j][i] (+)= sum_{p in [seg[j], seg[j+1])} coef[p] * Y[p][i]
+template <class T>
+__global__ void seg_sum_kernel(const T* __restrict__ Y, const int* __restrict__ seg,
+                               const double* __restrict__ coef, T* __restrict__ out, int n_out,
+                               long long size, int accumulate) {
+  const long long total = (long long)n_out * size;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / size);
+    const long long i = idx - (long long)j * size;
+    T acc = accumulate ? out[idx] : T(0);
+    for (int p = seg[j]; p < seg[j + 1]; ++p) acc += (T)coef[p] * Y[(long long)p * size + i];
+    out[idx] = acc;
+  }
+}
+
+// ---- MINRES (batched over states; scalars in float64) ----------------------------------------
+enum { MR_BETA1, MR_BNORM, MR_BETA, MR_C1, MR_S1, MR_C2, MR_S2, MR_PHIBAR, MR_ACTIVE, MR_ALPHA,
+       MR_BNEXT2, MR_DELTA, MR_EPS, MR_GAMMA, MR_TAU, MR_BNEXT, MR_UPD, MR_CONT, MR_ITS,
+       MR_HITCAP, MR_NFIELDS };
+
+__global__ void mr_init_scalars(double* sc, const double* bb, const double* rr, int n) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double* f = sc + (long long)s * MR_NFIELDS;
+  const double beta1 = sqrt(fmax(rr[s], 0.0)), bnorm = sqrt(fmax(bb[s], 0.0));
+  f[MR_BETA1] = beta1;
+  f[MR_BNORM] = bnorm;
+  f[MR_BETA] = beta1;
+  f[MR_C1] = 1.0;
+  f[MR_S1] = 0.0;
+  f[MR_C2] = 1.0;
+  f[MR_S2] = 0.0;
+  f[MR_PHIBAR] = beta1;
+  f[MR_ACTIVE] = (beta1 > 0.0 && bnorm > 0.0) ? 1.0 : 0.0;
+  f[MR_ITS] = 0.0;
+  f[MR_HITCAP] = 0.0;
+}
+
+// r = b - Ax (in p), v = r / beta1, vp = 0, w1 = w2 = 0
+template <class T>
+__global__ void mr_init_vectors(const double* sc, const T* b, const T* Ax, T* v, T* vp, T* w1,
+                                T* w2, long long n, int n_states) {
+  const long long total = n * n_states;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double* f = sc + (idx / n) * MR_NFIELDS;
+    const double beta1 = f[MR_BETA1];
+    const T r = b[idx] - Ax[idx];
+    v[idx] = beta1 > 0.0 ? (T)((double)r / beta1) : T(0);
+    vp[idx] = T(0);
+    w1[idx] = T(0);
+    w2[idx] = T(0);
+  }
+}
+
+// r = b - Ax stored into Ax's buffer (for the initial residual norm)
+template <class T>
+__global__ void sub_kernel(const T* b, T* Ax, long long total) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x)
+    Ax[idx] = b[idx] - Ax[idx];
+}
+
+// p = p - alpha v - beta vp
+template <class T>
+__global__ void mr_lanczos(const double* sc, const double* alpha, T* p, const T* v, const T* vp,
+                           long long n, int n_states) {
+  const long long total = n * n_states;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long s = idx / n;
+    const double* f = sc + s * MR_NFIELDS;
+    p[idx] = (T)((double)p[idx] - alpha[s] * (double)v[idx] - f[MR_BETA] * (double)vp[idx]);
+  }
+}
+
+__global__ void mr_step_scalars(double* sc, const double* alpha, const double* bnext2, int n,
+                                double tol, int maxiter) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double* f = sc + (long long)s * MR_NFIELDS;
+  f[MR_UPD] = 0.0;
+  f[MR_CONT] = 0.0;
+  if (f[MR_ACTIVE] == 0.0) return;
+  const double a = alpha[s], beta = f[MR_BETA];
+  const double bnext = sqrt(fmax(bnext2[s], 0.0));
+  const double eps = f[MR_S2] * beta;
+  const double dtil = f[MR_C2] * beta;
+  const double delta = f[MR_C1] * dtil + f[MR_S1] * a;
+  const double gtil = -f[MR_S1] * dtil + f[MR_C1] * a;
+  const double gamma = hypot(gtil, bnext);
+  f[MR_ITS] += 1.0;
+  if (gamma == 0.0) {
+    f[MR_ACTIVE] = 0.0;
+    return;
+  }
+  const double c = gtil / gamma, sn = bnext / gamma;
+  const double tau = c * f[MR_PHIBAR];
+  f[MR_PHIBAR] = -sn * f[MR_PHIBAR];
+  f[MR_DELTA] = delta;
+  f[MR_EPS] = eps;
+  f[MR_GAMMA] = gamma;
+  f[MR_TAU] = tau;
+  f[MR_BNEXT] = bnext;
+  f[MR_C2] = f[MR_C1];
+  f[MR_S2] = f[MR_S1];
+  f[MR_C1] = c;
+  f[MR_S1] = sn;
+  f[MR_UPD] = 1.0;
+  const bool conv = bnext == 0.0 || fabs(f[MR_PHIBAR]) <= tol * f[MR_BNORM];
+  f[MR_CONT] = conv ? 0.0 : 1.0;
+  f[MR_ACTIVE] = conv ? 0.0 : 1.0;
+  if (!conv && f[MR_ITS] >= maxiter) f[MR_HITCAP] = 1.0;
+  f[MR_BETA] = bnext;
+}
+
+template <class T>
+__global__ void mr_step_vectors(const double* sc, T* x, T* v, T* vp, T* w1, T* w2, const T* p,
+                                long long n, int n_states) {
+  const long long total = n * n_states;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const double* f = sc + (idx / n) * MR_NFIELDS;
+    if (f[MR_UPD] == 0.0) continue;
+    const double wn = ((double)v[idx] - f[MR_DELTA] * (double)w1[idx] -
+                       f[MR_EPS] * (double)w2[idx]) / f[MR_GAMMA];
+    x[idx] = (T)((double)x[idx] + f[MR_TAU] * wn);
+    w2[idx] = w1[idx];
+    w1[idx] = (T)wn;
+    if (f[MR_CONT] != 0.0) {
+      vp[idx] = v[idx];
+      v[idx] = (T)((double)p[idx] / f[MR_BNEXT]);
+    }
+  }
+}
+
+// ---- Rayleigh-Ritz: cyclic Jacobi (round-robin parallel ordering), one CTA, float64 ---------
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int m, int max_sweeps,
+                                                      double tol) {
+  extern __shared__ double sh[];
+  const int mp = m + (m & 1);
+  const int npairs = mp / 2;
+  double* cs = sh;              // npairs
+  double* sn = sh + npairs;     // npairs
+  int* pp = reinterpret_cast<int*>(sh + 2 * npairs);
+  int* qq = pp + npairs;
+  __shared__ double red[33];
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
+    V[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const double a = A[idx];
+      tot += a * a;
+      if (idx / m != idx % m) off += a * a;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (off <= tol * tol * tot) break;
+    for (int r = 0; r < mp - 1; ++r) {
+      for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
+        int p, q;
+        if (i == 0) {
+          p = 0;
+          q = (r % (mp - 1)) + 1;
+        } else {
+          p = ((i + r) % (mp - 1)) + 1;
+          q = ((mp - 1 - i + r) % (mp - 1)) + 1;
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        pp[i] = p;
+        qq[i] = q;
+        double c = 1.0, s = 0.0;
+        if (q < m) {
+          const double apq = A[p * m + q];
+          if (apq != 0.0) {
+            const double theta = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = threadIdx.x; idx < npairs * m; idx += blockDim.x) {
+        const int i = idx / m, j = idx % m;
+        const int p = pp[i], q = qq[i];
+        if (q >= m || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = A[p * m + j], aq = A[q * m + j];
+        A[p * m + j] = c * ap - s * aq;
+        A[q * m + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = threadIdx.x; idx < npairs * m; idx += blockDim.x) {
+        const int i = idx / m, j = idx % m;
+        const int p = pp[i], q = qq[i];
+        if (q >= m || sn[i] == 0.0) continue;
+        const double c = cs[i], s = sn[i];
+        const double ap = A[j * m + p], aq = A[j * m + q];
+        A[j * m + p] = c * ap - s * aq;
+        A[j * m + q] = s * ap + c * aq;
+        const double vp = V[j * m + p], vq = V[j * m + q];
+        V[j * m + p] = c * vp - s * vq;
+        V[j * m + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Sort eigenpairs ascending (stable in index), sign convention: the largest-|.| entry of each
+// eigenvector (first on ties) is positive. evals[i] = A[i][i]; Vout columns sorted.
+__global__ void sort_eig_kernel(const double* A, const double* V, int m, double* evals,
+                                double* Vout) {
+  extern __shared__ int rank[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double ei = A[i * m + i];
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      const double ej = A[j * m + j];
+      if (ej < ei || (ej == ei && j < i)) ++r;
+    }
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int r = rank[i];
+    evals[r] = A[i * m + i];
+    int arg = 0;
+    double best = -1.0;
+    for (int j = 0; j < m; ++j)
+      if (fabs(V[j * m + i]) > best) {
+        best = fabs(V[j * m + i]);
+        arg = j;
+      }
+    const double sg = V[arg * m + i] < 0.0 ? -1.0 : 1.0;
+    for (int j = 0; j < m; ++j) Vout[j * m + r] = sg * V[j * m + i];
+  }
+}
+
+// C (m1 x n1) = op(A)^T-free small dense products in float64: C[i][j] = sum_k A[i*sa + k*ka] *
+// B[k*sb + j*jb]
+__global__ void small_gemm_kernel(const double* A, long long a_i, long long a_k, const double* B,
+                                  long long b_k, long long b_j, double* C, int m1, int n1, int K) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m1 * n1;
+       idx += gridDim.x * blockDim.x) {
+    const int i = idx / n1, j = idx % n1;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) acc += A[i * a_i + k * a_k] * B[k * b_k + j * b_j];
+    C[idx] = acc;
+  }
+}
+
+// X[:, c] = U[:, keep[c]] / sqrt(mu[keep[c]])
+__global__ void canon_basis_kernel(const double* U, const double* mu, const int* keep, int m,
+                                   int k, double* X) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * k;
+       idx += gridDim.x * blockDim.x) {
+    const int i = idx / k, c = idx % k;
+    X[idx] = U[i * m + keep[c]] / sqrt(mu[keep[c]]);
+  }
+}
+
+// Sign convention of the Ritz vectors: the largest-|.| entry of each column (first on ties) is
+// made positive. V is m x n row-major; one thread per column.
+__global__ void fix_sign_kernel(double* V, int m, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int arg = 0;
+  double best = -1.0;
+  for (int i = 0; i < m; ++i)
+    if (fabs(V[(long long)i * n + j]) > best) {
+      best = fabs(V[(long long)i * n + j]);
+      arg = i;
+    }
+  if (V[(long long)arg * n + j] < 0.0)
+    for (int i = 0; i < m; ++i) V[(long long)i * n + j] = -V[(long long)i * n + j];
+}
+
+__global__ void symmetrize_kernel(double* A, int m) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m;
+       idx += gridDim.x * blockDim.x) {
+    const int i = idx / m, j = idx % m;
+    if (i < j) {
+      const double v = 0.5 * (A[i * m + j] + A[j * m + i]);
+      A[i * m + j] = v;
+      A[j * m + i] = v;
+    }
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// host-side drivers
+// ------------------------------------------------------------------------------------------------
+template <class T> T* work_node(ttn_block* b, int t);
+template <> double* work_node<double>(ttn_block* b, int t) {
+  b->touch();
+  return b->node64(t);
+}
+template <> float* work_node<float>(ttn_block* b, int t) {
+  b->node32(t);
+  return b->d32.as<float>() + b->off[t];
+}
+template <class T> void commit(ttn_block* b);
+template <> void commit<double>(ttn_block* b) { b->touch(); }
+template <> void commit<float>(ttn_block* b) {
+  b->node32(0);
+  launch_to_f64(b->ctx, b->d32.as<float>(), b->d64.as<double>(), b->total);
+  b->f32_valid = true;
+}
+
+struct DevVec {
+  DevBuf buf;
+  int maxv = 0;
+  int n = 0;
+  DevVec() = default;
+  template <class V>
+  DevVec(const std::vector<V>& v, cudaStream_t s)
+      : buf(std::max<size_t>(v.size(), 1) * sizeof(V), s), n((int)v.size()) {
+    if (!v.empty())
+      CUDA_CHECK(cudaMemcpyAsync(buf.p, v.data(), v.size() * sizeof(V), cudaMemcpyHostToDevice,
+                                 s));
+  }
+};
+
+static PairSet make_pairs(const std::vector<int>& pb, const std::vector<int>& pk, DevVec& db,
+                          DevVec& dk, cudaStream_t s) {
+  db = DevVec(pb, s);
+  dk = DevVec(pk, s);
+  PairSet ps;
+  ps.P = (int)pb.size();
+  ps.d_pb = db.buf.as<int>();
+  ps.d_pk = dk.buf.as<int>();
+  for (int x : pb) ps.max_bra = std::max(ps.max_bra, x);
+  for (int x : pk) ps.max_ket = std::max(ps.max_ket, x);
+  return ps;
+}
+
+// Environments of <bra|H|ket> over a fixed pair list, computed on demand and invalidated when
+// node tensors change (an up environment depends on the subtree below its edge, a down
+// environment on everything outside it).
+template <class T>
+struct EnvCache {
+  ttn_ctx* ctx = nullptr;
+  ttn_ttno* H = nullptr;
+  const ttn_block* bra = nullptr;
+  const ttn_block* ket = nullptr;
+  PairSet ps;
+  DevVec dpb, dpk;
+  const TreeInfo* tr = nullptr;
+  std::vector<DevBuf> up, down;
+  std::vector<char> up_ok, down_ok;
+  std::vector<std::vector<char>> in_sub;
+
+  void init(ttn_ctx* c, ttn_ttno* h, const ttn_block* b, const ttn_block* k,
+            const std::vector<int>& pb, const std::vector<int>& pk) {
+    ctx = c;
+    H = h;
+    bra = b;
+    ket = k;
+    tr = &b->tree;
+    ps = make_pairs(pb, pk, dpb, dpk, c->stream);
+    up.clear();
+    down.clear();
+    up.resize(tr->n);
+    down.resize(tr->n);
+    up_ok.assign(tr->n, 0);
+    down_ok.assign(tr->n, 0);
+    in_sub.assign(tr->n, std::vector<char>(tr->n, 0));
+    for (int e = 0; e < tr->n; ++e) {
+      std::vector<int> st{e};
+      while (!st.empty()) {
+        int u = st.back();
+        st.pop_back();
+        in_sub[e][u] = 1;
+        for (int ch : tr->children[u]) st.push_back(ch);
+      }
+    }
+  }
+  long long esize(int e) const { return (long long)H->wbond[e] * bra->bond[e] * ket->bond[e]; }
+  void invalidate(int u) {
+    for (int e = 0; e < tr->n; ++e) {
+      if (e == tr->root) continue;
+      if (in_sub[e][u]) up_ok[e] = 0;
+      else down_ok[e] = 0;
+    }
+  }
+  const T* get_up(int e) {
+    if (!up_ok[e]) {
+      const int nl = tr->nlegs(e);
+      std::vector<const T*> env(nl, nullptr);
+      for (int m = 1; m < nl; ++m) env[m] = get_up(tr->legs[e][m]);
+      const long long n = (long long)ps.P * esize(e);
+      if (!up[e].p) up[e] = DevBuf((size_t)n * sizeof(T), ctx->stream);
+      node_op<T>(ctx, H, e, 0, bra, ket, ps, env, {}, up[e].p, n, OUT_ENV);
+      up_ok[e] = 1;
+    }
+    return up[e].as<T>();
+  }
+  const T* get_down(int e) {
+    if (!down_ok[e]) {
+      const int u = tr->parent[e];
+      const int nl = tr->nlegs(u);
+      const int m = tr->leg_to(u, e);
+      std::vector<const T*> env(nl, nullptr);
+      const int off = u == tr->root ? 0 : 1;
+      if (off) env[0] = get_down(u);
+      for (int m2 = off; m2 < nl; ++m2)
+        if (m2 != m) env[m2] = get_up(tr->legs[u][m2]);
+      const long long n = (long long)ps.P * esize(e);
+      if (!down[e].p) down[e] = DevBuf((size_t)n * sizeof(T), ctx->stream);
+      node_op<T>(ctx, H, u, m, bra, ket, ps, env, {}, down[e].p, n, OUT_ENV);
+      down_ok[e] = 1;
+    }
+    return down[e].as<T>();
+  }
+  std::vector<const T*> node_envs(int t) {
+    const int nl = tr->nlegs(t);
+    std::vector<const T*> env(nl);
+    for (int m = 0; m < nl; ++m) {
+      const int nb = tr->legs[t][m];
+      env[m] = tr->parent[t] == nb ? get_down(t) : get_up(nb);
+    }
+    return env;
+  }
+};
+
+// Move the orthogonality centre of every state of `b` from node u to its neighbour v.
+template <class T>
+static void qr_move(ttn_ctx* ctx, ttn_block* b, int u, int v) {
+  const TreeInfo& tr = b->tree;
+  cudaStream_t st = ctx->stream;
+  const int n = b->n_states;
+  if (n == 0) return;
+  const int nl = tr.nlegs(u);
+  const int m = tr.leg_to(u, v);
+  const int D = b->bdim(u, m);
+  const long long size = b->size[u];
+  const long long rows = size / D;
+  TTN_REQUIRE(rows >= D, "gauge move %d->%d: bond %d exceeds the rest of the node (%lld)", u, v,
+              D, rows);
+  TTN_REQUIRE(D <= 64, "gauge move: bonds above 64 are not supported (%d)", D);
+  std::vector<int> dims(b->dims[u].begin(), b->dims[u].end());   // legs..., phys
+  std::vector<int> perm;
+  for (int k = 0; k <= nl; ++k)
+    if (k != m) perm.push_back(k);
+  perm.push_back(m);
+  T* node = work_node<T>(b, u);
+  DevBuf M((size_t)n * size * sizeof(T), st), Q((size_t)n * size * sizeof(T), st),
+      R((size_t)n * D * D * sizeof(T), st);
+  launch_permute<T>(ctx, node, M.as<T>(), n, nl + 1, dims.data(), perm.data());
+  {
+    LaunchScope ls(ctx, sizeof(T) == 8 ? "householder_qr_f64" : "householder_qr_f32",
+                   4.0 * rows * D * D * n, 4.0 * sizeof(T) * size * n);
+    householder_qr_kernel<T><<<n, kT, 0, st>>>(M.as<T>(), Q.as<T>(), R.as<T>(), (int)rows, D,
+                                               size);
+    CUDA_LAUNCH_CHECK();
+  }
+  std::vector<int> pdims(nl + 1), inv(nl + 1);
+  for (int k = 0; k <= nl; ++k) {
+    pdims[k] = dims[perm[k]];
+    inv[perm[k]] = k;
+  }
+  launch_permute<T>(ctx, Q.as<T>(), node, n, nl + 1, pdims.data(), inv.data());
+  // absorb R into v's leg toward u
+  const int mv = tr.leg_to(v, u);
+  long long inner = 1;
+  for (size_t k = mv + 1; k < b->dims[v].size(); ++k) inner *= b->dims[v][k];
+  const long long vsize = b->size[v];
+  T* vnode = work_node<T>(b, v);
+  DevBuf tmp((size_t)n * vsize * sizeof(T), st);
+  {
+    LaunchScope ls(ctx, "leg_product", 2.0 * D * vsize * n, 2.0 * sizeof(T) * vsize * n);
+    leg_product_kernel<T><<<grid_of((long long)n * vsize), kT, 0, st>>>(
+        R.as<T>(), vnode, tmp.as<T>(), n, vsize, inner, D);
+    CUDA_LAUNCH_CHECK();
+  }
+  CUDA_CHECK(cudaMemcpyAsync(vnode, tmp.p, (size_t)n * vsize * sizeof(T),
+                             cudaMemcpyDeviceToDevice, st));
+}
+
+template <class T>
+static void canonicalize(ttn_ctx* ctx, ttn_block* b) {
+  for (int c : b->tree.post)
+    if (c != b->tree.root) qr_move<T>(ctx, b, c, b->tree.parent[c]);
+}
+
+template <class T, class F>
+static int move_center(ttn_ctx* ctx, ttn_block* b, int from, int to, F&& on_change) {
+  std::vector<int> p = b->tree.path(from, to);
+  for (size_t k = 0; k + 1 < p.size(); ++k) {
+    qr_move<T>(ctx, b, p[k], p[k + 1]);
+    on_change(p[k]);
+    on_change(p[k + 1]);
+  }
+  return to;
+}
+
+template <class T>
+static void launch_dot(ttn_ctx* ctx, const T* x, const T* y, long long n, int n_states,
+                       double* out) {
+  if (n_states == 0) return;
+  LaunchScope ls(ctx, "dot", 2.0 * n * n_states, 2.0 * sizeof(T) * n * n_states);
+  dot_kernel<T><<<n_states, kT, 0, ctx->stream>>>(x, y, n, out);
+  CUDA_LAUNCH_CHECK();
+}
+
+template <class T>
+static void launch_scale(ttn_ctx* ctx, T* x, const double* f, long long n, int mode,
+                         int n_states) {
+  if (n_states == 0) return;
+  LaunchScope ls(ctx, "scale", 1.0 * n * n_states, 2.0 * sizeof(T) * n * n_states);
+  scale_kernel<T><<<grid_of(n * n_states), kT, 0, ctx->stream>>>(x, f, n, mode, n_states);
+  CUDA_LAUNCH_CHECK();
+}
+
+// Batched MINRES on (H_eff,t - shift_s) x_s = b_s for all states s; x holds the warm start.
+// Returns true if some state hit maxiter without reaching the tolerance.
+template <class T>
+static bool minres_batched(ttn_ctx* ctx, ttn_ttno* H, EnvCache<T>& env, int t,
+                           const ttn_block* shape, T* x, const T* b, const double* d_shift,
+                           int n, int maxiter, double tol) {
+  cudaStream_t st = ctx->stream;
+  const long long sz = shape->size[t];
+  const long long total = sz * n;
+  std::vector<DevBuf> bufs;
+  for (int i = 0; i < 5; ++i) bufs.emplace_back((size_t)std::max<long long>(total, 1) * sizeof(T), st);
+  T* p = bufs[0].as<T>();
+  T* v = bufs[1].as<T>();
+  T* vp = bufs[2].as<T>();
+  T* w1 = bufs[3].as<T>();
+  T* w2 = bufs[4].as<T>();
+  DevBuf sc((size_t)n * MR_NFIELDS * sizeof(double), st), d1(n * sizeof(double), st),
+      d2(n * sizeof(double), st);
+  std::vector<const T*> envs = env.node_envs(t);
+  std::vector<int> da(shape->tree.nlegs(t));
+  for (int m = 0; m < (int)da.size(); ++m) da[m] = shape->bdim(t, m);
+  auto matvec = [&](const T* in, T* out) {
+    node_op<T>(ctx, H, t, -1, nullptr, shape, env.ps, envs, da, out, total, OUT_LOCAL, in, n);
+    launch_shift_axpy<T>(ctx, out, in, d_shift, n, sz);
+  };
+  matvec(x, p);
+  {
+    LaunchScope ls(ctx, "minres_vec", 1.0 * total, 3.0 * sizeof(T) * total);
+    sub_kernel<T><<<grid_of(total), kT, 0, st>>>(b, p, total);
+    CUDA_LAUNCH_CHECK();
+  }
+  launch_dot<T>(ctx, b, b, sz, n, d1.as<double>());
+  launch_dot<T>(ctx, p, p, sz, n, d2.as<double>());
+  {
+    LaunchScope ls(ctx, "minres_scalar", 0.0, 0.0);
+    mr_init_scalars<<<(n + 127) / 128, 128, 0, st>>>(sc.as<double>(), d1.as<double>(),
+                                                     d2.as<double>(), n);
+    CUDA_LAUNCH_CHECK();
+  }
+  {
+    // p holds r = b - A x0; rebuild the recurrence vectors from it (b - (b - r) = r)
+    LaunchScope ls(ctx, "minres_vec", 1.0 * total, 6.0 * sizeof(T) * total);
+    DevBuf zero((size_t)std::max<long long>(total, 1) * sizeof(T), st);
+    CUDA_CHECK(cudaMemsetAsync(zero.p, 0, total * sizeof(T), st));
+    mr_init_vectors<T><<<grid_of(total), kT, 0, st>>>(sc.as<double>(), p, zero.as<T>(), v, vp,
+                                                      w1, w2, sz, n);
+    CUDA_LAUNCH_CHECK();
+  }
+  for (int it = 0; it < maxiter; ++it) {
+    matvec(v, p);
+    launch_dot<T>(ctx, v, p, sz, n, d1.as<double>());
+    {
+      LaunchScope ls(ctx, "minres_vec", 4.0 * total, 4.0 * sizeof(T) * total);
+      mr_lanczos<T><<<grid_of(total), kT, 0, st>>>(sc.as<double>(), d1.as<double>(), p, v, vp,
+                                                   sz, n);
+      CUDA_LAUNCH_CHECK();
+    }
+    launch_dot<T>(ctx, p, p, sz, n, d2.as<double>());
+    {
+      LaunchScope ls(ctx, "minres_scalar", 0.0, 0.0);
+      mr_step_scalars<<<(n + 127) / 128, 128, 0, st>>>(sc.as<double>(), d1.as<double>(),
+                                                       d2.as<double>(), n, tol, maxiter);
+      CUDA_LAUNCH_CHECK();
+    }
+    {
+      LaunchScope ls(ctx, "minres_vec", 8.0 * total, 8.0 * sizeof(T) * total);
+      mr_step_vectors<T><<<grid_of(total), kT, 0, st>>>(sc.as<double>(), x, v, vp, w1, w2, p,
+                                                        sz, n);
+      CUDA_LAUNCH_CHECK();
+    }
+    if (maxiter > 32 && (it + 1) % 16 == 0) {
+      std::vector<double> h((size_t)n * MR_NFIELDS);
+      CUDA_CHECK(cudaMemcpyAsync(h.data(), sc.p, h.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int s = 0; s < n; ++s) any |= h[(size_t)s * MR_NFIELDS + MR_ACTIVE] != 0.0;
+      if (!any) break;
+    }
+  }
+  std::vector<double> h((size_t)n * MR_NFIELDS);
+  CUDA_CHECK(cudaMemcpyAsync(h.data(), sc.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  bool hit = false;
+  for (int s = 0; s < n; ++s) {
+    const double* f = h.data() + (size_t)s * MR_NFIELDS;
+    hit |= f[MR_ACTIVE] != 0.0 || f[MR_HITCAP] != 0.0;
+  }
+  return hit;
+}
+
+// ALS (Sec. II.C.3): y_s <- argmin over one node at a time of |(H - shift_s) y_s - rhs_s|.
+template <class T>
+static bool als_impl(ttn_ctx* ctx, ttn_ttno* H, const std::vector<double>& shift,
+                     const ttn_block* rhs, ttn_block* y, int n_sweeps, int mr_max,
+                     double mr_tol) {
+  const TreeInfo& tr = y->tree;
+  const int n = y->n_states;
+  cudaStream_t st = ctx->stream;
+  std::vector<int> id(n);
+  std::iota(id.begin(), id.end(), 0);
+  canonicalize<T>(ctx, y);
+  int center = tr.root;
+  EnvCache<T> eH, eS;
+  eH.init(ctx, H, y, y, id, id);
+  eS.init(ctx, identity_for(ctx, tr), y, rhs, id, id);
+  DevVec dshift(shift, st);
+  bool hit = false;
+  for (int sweep = 0; sweep < n_sweeps; ++sweep) {
+    for (int t : tr.pre) {
+      center = move_center<T>(ctx, y, center, t, [&](int u) {
+        eH.invalidate(u);
+        eS.invalidate(u);
+      });
+      const long long sz = y->size[t];
+      DevBuf bvec((size_t)std::max<long long>(sz * n, 1) * sizeof(T), st);
+      std::vector<int> da(tr.nlegs(t));
+      for (int m = 0; m < (int)da.size(); ++m) da[m] = y->bdim(t, m);
+      node_op<T>(ctx, eS.H, t, -1, nullptr, rhs, eS.ps, eS.node_envs(t), da, bvec.p, sz * n,
+                 OUT_LOCAL);
+      T* x = work_node<T>(y, t);
+      hit |= minres_batched<T>(ctx, H, eH, t, y, x, bvec.as<T>(), dshift.buf.as<double>(), n,
+                               mr_max, mr_tol);
+      eH.invalidate(t);
+      eS.invalidate(t);
+    }
+  }
+  commit<T>(y);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  return hit;
+}
+
+struct FitGroup {
+  ttn_ttno* op;
+  const ttn_block* in;
+  std::vector<int> out_j, in_k;   // pairs, sorted by out_j
+  std::vector<double> coef;
+};
+
+// Variational fitting (Sec. II.C.2): in canonical gauge the local solution at the centre is
+// the right-hand side sum_i c_i <psi without t| O_i |phi_i>.
+template <class T>
+static void fit_impl(ttn_ctx* ctx, std::vector<FitGroup>& groups, ttn_block* out, int n_sweeps) {
+  const TreeInfo& tr = out->tree;
+  const int n_out = out->n_states;
+  cudaStream_t st = ctx->stream;
+  canonicalize<T>(ctx, out);
+  int center = tr.root;
+  std::vector<EnvCache<T>> caches(groups.size());
+  std::vector<DevVec> seg(groups.size()), coef(groups.size());
+  for (size_t g = 0; g < groups.size(); ++g) {
+    caches[g].init(ctx, groups[g].op, out, groups[g].in, groups[g].out_j, groups[g].in_k);
+    std::vector<int> sp(n_out + 1, 0);
+    for (int j : groups[g].out_j) sp[j + 1]++;
+    for (int j = 0; j < n_out; ++j) sp[j + 1] += sp[j];
+    seg[g] = DevVec(sp, st);
+    coef[g] = DevVec(groups[g].coef, st);
+  }
+  for (int sweep = 0; sweep < n_sweeps; ++sweep) {
+    for (int t : tr.pre) {
+      center = move_center<T>(ctx, out, center, t, [&](int u) {
+        for (auto& c : caches) c.invalidate(u);
+      });
+      const long long sz = out->size[t];
+      DevBuf acc((size_t)std::max<long long>(sz * n_out, 1) * sizeof(T), st);
+      CUDA_CHECK(cudaMemsetAsync(acc.p, 0, (size_t)sz * n_out * sizeof(T), st));
+      std::vector<int> da(tr.nlegs(t));
+      for (int m = 0; m < (int)da.size(); ++m) da[m] = out->bdim(t, m);
+      for (size_t g = 0; g < groups.size(); ++g) {
+        const int P = caches[g].ps.P;
+        if (P == 0) continue;
+        DevBuf Y((size_t)P * sz * sizeof(T), st);
+        node_op<T>(ctx, groups[g].op, t, -1, nullptr, groups[g].in, caches[g].ps,
+                   caches[g].node_envs(t), da, Y.p, (long long)P * sz, OUT_LOCAL);
+        LaunchScope ls(ctx, "seg_sum", 2.0 * P * sz, sizeof(T) * ((double)P * sz + 2.0 * n_out * sz));
+        seg_sum_kernel<T><<<grid_of(sz * n_out), kT, 0, st>>>(
+            Y.as<T>(), seg[g].buf.as<int>(), coef[g].buf.as<double>(), acc.as<T>(), n_out, sz, 1);
+        CUDA_LAUNCH_CHECK();
+      }
+      T* node = work_node<T>(out, t);
+      CUDA_CHECK(cudaMemcpyAsync(node, acc.p, (size_t)sz * n_out * sizeof(T),
+                                 cudaMemcpyDeviceToDevice, st));
+      for (auto& c : caches) c.invalidate(t);
+    }
+  }
+  commit<T>(out);
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+// Scale every state to unit norm (the norm is taken over the whole network).
+template <class T>
+static void normalize_states(ttn_ctx* ctx, ttn_block* b, int prec) {
+  const int n = b->n_states;
+  DevBuf S((size_t)n * sizeof(double), ctx->stream);
+  std::vector<int> id(n);
+  std::iota(id.begin(), id.end(), 0);
+  gram_pairs<T>(ctx, identity_for(ctx, b->tree), b, b, id, id, S.as<double>());
+  (void)prec;
+  launch_scale<double>(ctx, b->node64(b->tree.root), S.as<double>(), b->size[b->tree.root], 1, n);
+  b->touch();
+  CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+}
+
+// Rayleigh-Ritz on device data (float64): theta[n], V[m x n] (device).
+static void rayleigh_ritz_device(ttn_ctx* ctx, int m, const double* dHt, const double* dMt,
+                                 int n, double eps, double* d_theta, double* dV) {
+  cudaStream_t st = ctx->stream;
+  TTN_REQUIRE(m >= 1 && n >= 1 && n <= m, "rayleigh_ritz: need 1 <= n <= m");
+  TTN_REQUIRE(m <= 2048, "rayleigh_ritz: m = %d too large", m);
+  const size_t mm = (size_t)m * m;
+  DevBuf A(mm * sizeof(double), st), U(mm * sizeof(double), st), Us(mm * sizeof(double), st),
+      mu(m * sizeof(double), st);
+  const int mp = m + (m & 1);
+  const size_t shj = (size_t)mp * sizeof(double) + (size_t)mp * sizeof(int) + 64;
+  auto eig = [&](double* Ain, int k, double* evals, double* Vout) {
+    {
+      LaunchScope ls(ctx, "symmetrize", 0.0, 16.0 * k * k);
+      symmetrize_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(Ain, k);
+      CUDA_LAUNCH_CHECK();
+    }
+    const int kp = k + (k & 1);
+    const size_t sh = (size_t)kp * sizeof(double) + (size_t)kp * sizeof(int) + 64;
+    {
+      LaunchScope ls(ctx, "jacobi_f64", 0.0, 0.0);
+      jacobi_kernel<<<1, 1024, sh, st>>>(Ain, U.as<double>(), k, 40, 1e-15);
+      CUDA_LAUNCH_CHECK();
+    }
+    {
+      LaunchScope ls(ctx, "sort_eig", 0.0, 0.0);
+      sort_eig_kernel<<<1, 256, k * sizeof(int), st>>>(Ain, U.as<double>(), k, evals, Vout);
+      CUDA_LAUNCH_CHECK();
+    }
+  };
+  (void)shj;
+  CUDA_CHECK(cudaMemcpyAsync(A.p, dMt, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  eig(A.as<double>(), m, mu.as<double>(), Us.as<double>());
+  std::vector<double> hmu(m);
+  CUDA_CHECK(cudaMemcpyAsync(hmu.data(), mu.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  for (double x : hmu)
+    if (!std::isfinite(x)) TTN_FAIL(TTN_ENONFINITE, "rayleigh_ritz: non-finite overlap matrix");
+  const double mx = *std::max_element(hmu.begin(), hmu.end());
+  std::vector<int> keep;
+  for (int i = 0; i < m; ++i)
+    if (hmu[i] > eps * mx) keep.push_back(i);
+  const int k = (int)keep.size();
+  TTN_REQUIRE(k >= n, "rayleigh_ritz: only %d of %d directions survive eps = %g", k, n, eps);
+  DevVec dkeep(keep, st);
+  DevBuf X((size_t)m * k * sizeof(double), st), HX((size_t)m * k * sizeof(double), st),
+      Hp((size_t)k * k * sizeof(double), st), th(k * sizeof(double), st),
+      Y((size_t)k * k * sizeof(double), st);
+  {
+    LaunchScope ls(ctx, "rr_small", 0.0, 0.0);
+    canon_basis_kernel<<<grid_of((long long)m * k), kT, 0, st>>>(Us.as<double>(), mu.as<double>(),
+                                                               dkeep.buf.as<int>(), m, k,
+                                                               X.as<double>());
+    CUDA_LAUNCH_CHECK();
+    // HX = Ht X   (m x k)
+    small_gemm_kernel<<<grid_of((long long)m * k), kT, 0, st>>>(dHt, m, 1, X.as<double>(), k, 1,
+                                                              HX.as<double>(), m, k, m);
+    // Hp = X^T HX (k x k)
+    small_gemm_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(X.as<double>(), 1, k,
+                                                              HX.as<double>(), k, 1,
+                                                              Hp.as<double>(), k, k, m);
+    CUDA_LAUNCH_CHECK();
+  }
+  eig(Hp.as<double>(), k, th.as<double>(), Y.as<double>());
+  {
+    LaunchScope ls(ctx, "rr_small", 0.0, 0.0);
+    // V = X Y[:, :n]   (m x n)
+    small_gemm_kernel<<<grid_of((long long)m * n), kT, 0, st>>>(X.as<double>(), k, 1,
+                                                              Y.as<double>(), k, 1, dV, m, n, k);
+    fix_sign_kernel<<<(n + 127) / 128, 128, 0, st>>>(dV, m, n);
+    CUDA_LAUNCH_CHECK();
+  }
+  CUDA_CHECK(cudaMemcpyAsync(d_theta, th.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+template <class F>
+static ttn_status guarded_s(ttn_ctx* ctx, F&& f) {
+  try {
+    ttn_status s = f();
+    ctx->last_error.clear();
+    return s;
+  } catch (const TtnError& e) {
+    ctx->last_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ctx->last_error = "host allocation failed";
+    return TTN_ENOMEM;
+  }
+}
+
+static void check_block_like(const ttn_block* a, const ttn_block* b) {
+  TTN_REQUIRE(a && b, "NULL block");
+  TTN_REQUIRE(a->tree.same_shape(b->tree) && a->bond == b->bond,
+              "blocks differ in tree or bond dimensions");
+}
+
+template <class T>
+static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, double shift_offset,
+                        int als_sweeps, int mr_max, double mr_tol, int fit_sweeps, int prec,
+                        double* eig_hist, bool& hit) {
+  const TreeInfo& tr = x->tree;
+  const int n = x->n_states;
+  cudaStream_t st = ctx->stream;
+  ttn_ttno* Id = identity_for(ctx, tr);
+  std::vector<int> id(n);
+  std::iota(id.begin(), id.end(), 0);
+  auto new_block = [&](int ns) {
+    ttn_tree tmp;
+    tmp.ctx = ctx;
+    tmp.info = tr;
+    ttn_block* b = nullptr;
+    ttn_status s = ttn_block_create(ctx, &tmp, ns, x->bond.data(), &b);
+    if (s != TTN_OK) TTN_FAIL(s, "%s", ctx->last_error.c_str());
+    return std::unique_ptr<ttn_block>(b);
+  };
+  normalize_states<T>(ctx, x, prec);
+  std::vector<double> lam(n);
+  {
+    DevBuf hv((size_t)n * sizeof(double), st), sv((size_t)n * sizeof(double), st);
+    gram_pairs<T>(ctx, H, x, x, id, id, hv.as<double>());
+    gram_pairs<T>(ctx, Id, x, x, id, id, sv.as<double>());
+    std::vector<double> h(n), s(n);
+    CUDA_CHECK(cudaMemcpyAsync(h.data(), hv.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(s.data(), sv.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    for (int j = 0; j < n; ++j) lam[j] = h[j] / s[j];
+  }
+  if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist);
+  auto R = new_block(n), Y = new_block(n), P = new_block(n), Xn = new_block(n), Pn = new_block(n);
+  bool have_p = false;
+  const double rr_eps = prec == TTN_FP64 ? 1e-12 : 1e-6;
+  for (int it = 1; it <= n_iter; ++it) {
+    const double s = *std::min_element(lam.begin(), lam.end()) + shift_offset;
+    // residual r_j = H x_j - lambda_j x_j by fitting, starting from x_j
+    {
+      std::vector<int> ids(n);
+      std::iota(ids.begin(), ids.end(), 0);
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      ttn_status cs = ttn_block_copy_states(R.get(), x, n, ids.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      std::vector<FitGroup> g(2);
+      g[0] = {H, x, id, id, std::vector<double>(n, 1.0)};
+      std::vector<double> ml(n);
+      for (int j = 0; j < n; ++j) ml[j] = -lam[j];
+      g[1] = {Id, x, id, id, ml};
+      fit_impl<T>(ctx, g, R.get(), fit_sweeps);
+    }
+    // preconditioner: (H - s) y = r by ALS, starting from r
+    {
+      std::vector<int> ids(n);
+      std::iota(ids.begin(), ids.end(), 0);
+      ttn_status cs = ttn_block_copy_states(Y.get(), R.get(), n, ids.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      hit |= als_impl<T>(ctx, H, std::vector<double>(n, s), R.get(), Y.get(), als_sweeps, mr_max,
+                         mr_tol);
+    }
+    // subspace S = {x} u {r} (u {p})
+    const int m = have_p ? 3 * n : 2 * n;
+    auto S = new_block(m);
+    {
+      std::vector<int> ids(n);
+      std::iota(ids.begin(), ids.end(), 0);
+      // gather into S by copying the three blocks' states
+      for (int j = 0; j < n; ++j) {
+        for (int t = 0; t < tr.n; ++t) {
+          const long long sz = x->size[t];
+          CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)j * sz, x->node64(t) + (long long)j * sz,
+                                     sz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)(n + j) * sz,
+                                     Y->node64(t) + (long long)j * sz, sz * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, st));
+          if (have_p)
+            CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)(2 * n + j) * sz,
+                                       P->node64(t) + (long long)j * sz, sz * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, st));
+        }
+      }
+      S->touch();
+    }
+    DevBuf Ht((size_t)m * m * sizeof(double), st), Mt((size_t)m * m * sizeof(double), st);
+    CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
+    CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
+    gram_device(ctx, H, S.get(), S.get(), Ht.as<double>(), m, prec);
+    gram_device(ctx, Id, S.get(), S.get(), Mt.as<double>(), m, prec);
+    DevBuf th((size_t)n * sizeof(double), st), V((size_t)m * n * sizeof(double), st);
+    rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), n, rr_eps, th.as<double>(),
+                         V.as<double>());
+    std::vector<double> hth(n), hV((size_t)m * n);
+    CUDA_CHECK(cudaMemcpyAsync(hth.data(), th.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(hV.data(), V.p, hV.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    // x_j = sum_k v_kj s_k (normalised), p_j = sum_{k >= n} v_kj s_k
+    auto fit_comb = [&](ttn_block* out, int k0) {
+      std::vector<int> init(n);
+      FitGroup g{Id, S.get(), {}, {}, {}};
+      for (int j = 0; j < n; ++j) {
+        int arg = k0;
+        double best = -1.0;
+        for (int k = k0; k < m; ++k) {
+          const double c = hV[(size_t)k * n + j];
+          if (std::fabs(c) > best) {
+            best = std::fabs(c);
+            arg = k;
+          }
+          if (c != 0.0) {
+            g.out_j.push_back(j);
+            g.in_k.push_back(k);
+            g.coef.push_back(c);
+          }
+        }
+        init[j] = arg;
+      }
+      ttn_status cs = ttn_block_copy_states(out, S.get(), n, init.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      std::vector<FitGroup> gs{g};
+      fit_impl<T>(ctx, gs, out, fit_sweeps);
+    };
+    fit_comb(Xn.get(), 0);
+    normalize_states<T>(ctx, Xn.get(), prec);
+    fit_comb(Pn.get(), n);
+    std::swap(P, Pn);
+    have_p = true;
+    {
+      std::vector<int> ids(n);
+      std::iota(ids.begin(), ids.end(), 0);
+      ttn_status cs = ttn_block_copy_states(x, Xn.get(), n, ids.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+    }
+    lam = hth;
+    if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist + (size_t)it * n);
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
 extern "C" {
 
-ttn_status ttn_recompress(ttn_ctx* ctx, int, const double*, const ttn_ttno* const*,
-                          const ttn_block* const*, const int*, ttn_block*, int, int,
-                          ttn_precision) {
-  if (ctx) ctx->last_error = "ttn_recompress: not built yet";
-  return TTN_EUNSUPPORTED;
+ttn_status ttn_recompress(ttn_ctx* ctx, int n_in, const double* coeff, const ttn_ttno* const* ops,
+                          const ttn_block* const* in, const int* in_state, ttn_block* out,
+                          int n_out, int n_sweeps, ttn_precision prec) {
+  if (!ctx || !out) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    TTN_REQUIRE(n_in >= 0 && (n_in == 0 || (coeff && ops && in && in_state)), "inputs");
+    TTN_REQUIRE(n_out == out->n_states, "n_out must equal the states of `out`");
+    TTN_REQUIRE(n_sweeps >= 0, "n_sweeps < 0");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    std::vector<FitGroup> groups;
+    for (int k = 0; k < n_in; ++k) {
+      check_block_like(in[k], out);
+      TTN_REQUIRE(in_state[k] >= 0 && in_state[k] < in[k]->n_states, "in_state[%d]", k);
+      ttn_ttno* op = ops[k] ? const_cast<ttn_ttno*>(ops[k]) : identity_for(ctx, out->tree);
+      if (ops[k]) TTN_REQUIRE(op->tree.same_shape(out->tree), "operator %d: other tree", k);
+      size_t g = 0;
+      for (; g < groups.size(); ++g)
+        if (groups[g].op == op && groups[g].in == in[k]) break;
+      if (g == groups.size()) groups.push_back({op, in[k], {}, {}, {}});
+    }
+    for (auto& g : groups) {
+      for (int j = 0; j < n_out; ++j)
+        for (int k = 0; k < n_in; ++k) {
+          ttn_ttno* op = ops[k] ? const_cast<ttn_ttno*>(ops[k]) : identity_for(ctx, out->tree);
+          const double c = coeff[(size_t)k * n_out + j];
+          if (op == g.op && in[k] == g.in && c != 0.0) {
+            g.out_j.push_back(j);
+            g.in_k.push_back(in_state[k]);
+            g.coef.push_back(c);
+          }
+        }
+    }
+    if (prec == TTN_FP64) fit_impl<double>(ctx, groups, out, n_sweeps);
+    else fit_impl<float>(ctx, groups, out, n_sweeps);
+    return TTN_OK;
+  });
 }
-ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno*, const double*, const ttn_block*,
-                         ttn_block*, int, int, double, ttn_precision) {
-  if (ctx) ctx->last_error = "ttn_als_solve: not built yet";
-  return TTN_EUNSUPPORTED;
+
+ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
+                         const ttn_block* rhs, ttn_block* y, int n_sweeps, int minres_max,
+                         double minres_tol, ttn_precision prec) {
+  if (!ctx || !H || !shift || !rhs || !y) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    check_block_like(rhs, y);
+    TTN_REQUIRE(rhs->n_states == y->n_states, "rhs and y differ in state count");
+    TTN_REQUIRE(H->tree.same_shape(y->tree), "operator on another tree");
+    TTN_REQUIRE(n_sweeps >= 0 && minres_max >= 0 && minres_tol >= 0.0, "bad solver settings");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    std::vector<double> s(shift, shift + y->n_states);
+    bool hit = prec == TTN_FP64
+                   ? als_impl<double>(ctx, const_cast<ttn_ttno*>(H), s, rhs, y, n_sweeps,
+                                      minres_max, minres_tol)
+                   : als_impl<float>(ctx, const_cast<ttn_ttno*>(H), s, rhs, y, n_sweeps,
+                                     minres_max, minres_tol);
+    return hit ? TTN_ENOTCONV : TTN_OK;
+  });
 }
-ttn_status ttn_rayleigh_ritz(ttn_ctx* ctx, int, const double*, const double*, int, double,
-                             double*, double*) {
-  if (ctx) ctx->last_error = "ttn_rayleigh_ritz: not built yet";
-  return TTN_EUNSUPPORTED;
+
+ttn_status ttn_rayleigh_ritz(ttn_ctx* ctx, int m, const double* Ht, const double* Mt, int n,
+                             double eps, double* theta, double* V) {
+  if (!ctx || !Ht || !Mt || !theta || !V) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    TTN_REQUIRE(m >= 1 && n >= 1 && n <= m, "need 1 <= n <= m");
+    cudaStream_t st = ctx->stream;
+    const size_t mm = (size_t)m * m;
+    DevBuf dH(mm * sizeof(double), st), dM(mm * sizeof(double), st), dth(n * sizeof(double), st),
+        dV((size_t)m * n * sizeof(double), st);
+    CUDA_CHECK(cudaMemcpyAsync(dH.p, Ht, mm * sizeof(double), cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(dM.p, Mt, mm * sizeof(double), cudaMemcpyHostToDevice, st));
+    rayleigh_ritz_device(ctx, m, dH.as<double>(), dM.as<double>(), n, eps, dth.as<double>(),
+                         dV.as<double>());
+    CUDA_CHECK(cudaMemcpyAsync(theta, dth.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(V, dV.p, (size_t)m * n * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return TTN_OK;
+  });
 }
-ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno*, ttn_block*, int, double, int, int, double,
-                      int, ttn_precision, double*) {
-  if (ctx) ctx->last_error = "ttn_lobpcg: not built yet";
-  return TTN_EUNSUPPORTED;
+
+ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
+                      double shift_offset, int als_sweeps, int minres_max, double minres_tol,
+                      int fit_sweeps, ttn_precision prec, double* eig_hist) {
+  if (!ctx || !H || !x) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    TTN_REQUIRE(n_iter >= 0 && als_sweeps >= 0 && minres_max >= 0 && fit_sweeps >= 0,
+                "bad solver settings");
+    TTN_REQUIRE(x->n_states >= 1, "empty block");
+    TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    bool hit = false;
+    if (prec == TTN_FP64)
+      lobpcg_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
+                          minres_max, minres_tol, fit_sweeps, prec, eig_hist, hit);
+    else
+      lobpcg_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
+                         minres_max, minres_tol, fit_sweeps, prec, eig_hist, hit);
+    return hit ? TTN_ENOTCONV : TTN_OK;
+  });
 }
 
 }  // extern "C"

@@ -35,6 +35,9 @@ _SIGS = {
     "ttn_last_error": (C.c_char_p, [_P]),
     "ttn_synchronize": (_I, [_P]),
     "ttn_launch_count": (_LL, [_P]),
+    "ttn_flop_count": (_D, [_P]),
+    "ttn_profile_enable": (_I, [_P, _I]),
+    "ttn_profile_get": (_I, [_P, _I, C.c_char_p, _LLP, _DP, _DP, _DP, _IP]),
     "ttn_tree_create": (_I, [_P, _I, _IP, _IP, C.POINTER(_P)]),
     "ttn_tree_destroy": (None, [_P]),
     "ttn_build_ttno": (_I, [_P, _P, _I, _IP, _LLP, _DP, _I, _DP, _IP, _IP, _D, C.POINTER(_P),
@@ -176,6 +179,30 @@ def ttn_synchronize(ctx):
 
 def ttn_launch_count(ctx) -> int:
     return int(load().ttn_launch_count(ctx.ptr))
+
+
+def ttn_flop_count(ctx) -> float:
+    return float(load().ttn_flop_count(ctx.ptr))
+
+
+def ttn_profile_enable(ctx, on=True):
+    ctx.check(load().ttn_profile_enable(ctx.ptr, 1 if on else 0))
+
+
+def ttn_profile_get(ctx, max_kernels=64):
+    """{kernel name: dict(launches, ms, flops, bytes)} since the last ttn_profile_enable."""
+    names = C.create_string_buffer(64 * max_kernels)
+    launches = np.zeros(max_kernels, dtype=np.int64)
+    ms, fl, by = np.zeros(max_kernels), np.zeros(max_kernels), np.zeros(max_kernels)
+    nk = C.c_int()
+    ctx.check(load().ttn_profile_get(ctx.ptr, max_kernels, names, _llp(launches), _dp(ms),
+                                     _dp(fl), _dp(by), C.byref(nk)))
+    out = {}
+    for i in range(min(nk.value, max_kernels)):
+        nm = names.raw[64 * i:64 * i + 64].split(b"\0")[0].decode()
+        out[nm] = dict(launches=int(launches[i]), ms=float(ms[i]), flops=float(fl[i]),
+                       bytes=float(by[i]))
+    return out
 
 
 def ttn_tree_create(ctx, tree) -> Tree:

@@ -1,0 +1,194 @@
+"""Parity of the GPU solver entry points (Rayleigh-Ritz, ALS, fitting, block LOBPCG) with the
+FP64 oracle on identical seeded inputs, and the LOBPCG end-to-end checks against dense exact
+diagonalisation (Alg. 2, Sec. II.C).
+
+MINRES runs with tolerance 0 in the parity cases so that both sides take exactly the same number
+of Krylov steps (a tolerance test could flip on a rounding difference); node tensors are then
+comparable because the gauge (QR with a non-negative R diagonal) is unique for full-rank nodes.
+FP64 tolerance 1e-10 relative (a few hundred dependent contractions and QR steps in float64);
+FP32 eigenvalues within 0.1 cm^-1 of the FP64 oracle (the accuracy target of the method)."""
+import numpy as np
+import pytest
+
+from oracle import network as N, solvers as S
+from paper_2512_15875_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2512_15875_gb300 import ttn
+    ttn.load()
+    return ttn
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.ttn_create(0)
+
+
+def _rel(x, ref):
+    return np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+def _states(blk, n):
+    return [[x[j] for x in blk] for j in range(n)]
+
+
+def _arrays(states):
+    return [np.stack([s[t] for s in states]) for t in range(len(states[0]))]
+
+
+@pytest.mark.parametrize("m,n", [(12, 4), (57, 7), (252, 84)])
+def test_rayleigh_ritz_matches_oracle(T, ctx, m, n):
+    rng = np.random.default_rng(m)
+    B = rng.standard_normal((m, m))
+    M = B @ B.T / m + 0.1 * np.eye(m)
+    H = rng.standard_normal((m, m))
+    H = H + H.T
+    th, V = T.ttn_rayleigh_ritz(ctx, H, M, n, 1e-12)
+    th_ref, V_ref = S.rayleigh_ritz(H, M, n)
+    assert _rel(th, th_ref) <= 1e-11
+    assert _rel(V, V_ref) <= 1e-8
+    assert np.abs(V.T @ M @ V - np.eye(n)).max() <= 1e-10
+
+
+def test_rayleigh_ritz_drops_null_directions(T, ctx):
+    rng = np.random.default_rng(5)
+    Q = np.linalg.qr(rng.standard_normal((10, 10)))[0]
+    mu = np.array([1.0, 2, 3, 4, 5, 6, 7, 8, 1e-15, 1e-16])
+    M = Q @ np.diag(mu) @ Q.T
+    H = rng.standard_normal((10, 10))
+    H = H + H.T
+    th, V = T.ttn_rayleigh_ritz(ctx, H, M, 3, 1e-12)
+    th_ref, _ = S.rayleigh_ritz(H, M, 3)
+    assert _rel(th, th_ref) <= 1e-10
+    with pytest.raises(T.TTNError):
+        T.ttn_rayleigh_ritz(ctx, H, M, 9, 1e-12)
+
+
+def _c1(T, ctx, D=8):
+    w = I.make_workload("c1", D=D)
+    th = T.ttn_tree_create(ctx, w.tree)
+    H, _ = T.ttn_build_ttno(ctx, th, w.ham.flat(w.tree))
+    return w, th, H
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fit_matches_oracle(T, ctx, prec):
+    w, th, H = _c1(T, ctx)
+    otn = N.build_ttno(w.tree, w.ham)
+    idt = N.identity_ttno(w.tree)
+    blk = w.block()
+    X = _states(blk, w.n_states)
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    out = T.ttn_block_create(ctx, th, 2, w.bonds)
+    T.ttn_block_copy_states(out, bX, [0, 3])
+    coeff = np.zeros((2 * w.n_states, 2))
+    # output 0: H x_0 - 1.5 x_0 ; output 1: 0.3 x_1 - 0.7 x_3 + 0.2 x_4
+    coeff[0, 0] = 1.0
+    coeff[w.n_states + 0, 0] = -1.5
+    coeff[w.n_states + 1, 1], coeff[w.n_states + 3, 1], coeff[w.n_states + 4, 1] = 0.3, -0.7, 0.2
+    ops = [H] * w.n_states + [None] * w.n_states
+    blocks = [bX] * (2 * w.n_states)
+    states = list(range(w.n_states)) * 2
+    T.ttn_recompress(ctx, coeff, ops, blocks, states, out, n_sweeps=2, prec=prec)
+    shp = [I.node_shape(w.tree, w.bonds, t) for t in range(w.tree.n_nodes)]
+    got = T.block_to_arrays(out, shp)
+    ref0 = S.fit(w.tree, [(1.0, otn, X[0]), (-1.5, idt, X[0])], X[0], 2)
+    ref1 = S.fit(w.tree, [(0.3, idt, X[1]), (-0.7, idt, X[3]), (0.2, idt, X[4])], X[3], 2)
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    for t in range(w.tree.n_nodes):
+        assert _rel(got[t][0], ref0[t]) <= tol, t
+        assert _rel(got[t][1], ref1[t]) <= tol, t
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_als_matches_oracle(T, ctx, prec):
+    w, th, H = _c1(T, ctx)
+    otn = N.build_ttno(w.tree, w.ham)
+    blk = w.block()
+    X = _states(blk, w.n_states)
+    bR = T.block_from_arrays(ctx, th, w.bonds, blk)
+    bY = T.block_from_arrays(ctx, th, w.bonds, blk)
+    lam0 = N.expectation(w.tree, otn, X[0], X[0]) / N.overlap(w.tree, X[0], X[0])
+    shifts = lam0 - 100.0 + 10.0 * np.arange(w.n_states)
+    T.ttn_als_solve(ctx, H, shifts, bR, bY, n_sweeps=2, minres_max=10, minres_tol=0.0, prec=prec)
+    shp = [I.node_shape(w.tree, w.bonds, t) for t in range(w.tree.n_nodes)]
+    got = T.block_to_arrays(bY, shp)
+    tol = 1e-10 if prec == "fp64" else 5e-3
+    for s in (0, 2, 4):
+        ref = S.als_solve(w.tree, otn, shifts[s], X[s], X[s], 2, 10, 0.0)
+        if prec == "fp64":
+            for t in range(w.tree.n_nodes):
+                assert _rel(got[t][s], ref[t]) <= tol, (s, t)
+        gv = N.ttns_to_dense(w.tree, [g[s] for g in got])
+        rv = N.ttns_to_dense(w.tree, ref)
+        assert _rel(gv, rv) <= tol, s
+
+
+def test_als_converges_to_the_exact_solve_at_full_bond(T, ctx):
+    w, th, H = _c1(T, ctx, D=36)
+    Hd = N.dense_hamiltonian(w.ham)
+    blk = w.block()
+    b = T.block_from_arrays(ctx, th, w.bonds, blk)
+    y = T.block_from_arrays(ctx, th, w.bonds, blk)
+    s = np.linalg.eigvalsh(Hd)[0] - 100.0
+    T.ttn_als_solve(ctx, H, np.full(w.n_states, s), b, y, n_sweeps=3, minres_max=400,
+                    minres_tol=1e-14)
+    shp = [I.node_shape(w.tree, w.bonds, t) for t in range(w.tree.n_nodes)]
+    got = T.block_to_arrays(y, shp)
+    for j in range(w.n_states):
+        yd = N.ttns_to_dense(w.tree, [g[j] for g in got])
+        rd = N.ttns_to_dense(w.tree, [x[j] for x in blk])
+        assert np.linalg.norm((Hd - s * np.eye(len(Hd))) @ yd - rd) <= 1e-9 * np.linalg.norm(rd)
+
+
+def test_lobpcg_matches_oracle_fp64(T, ctx):
+    w, th, H = _c1(T, ctx)
+    otn = N.build_ttno(w.tree, w.ham)
+    blk = w.block()
+    X0 = _states(blk, w.n_states)
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    n_iter = 3
+    hist = T.ttn_lobpcg(ctx, H, bX, n_iter, -100.0, als_sweeps=2, minres_max=10, minres_tol=0.0,
+                        fit_sweeps=2, prec="fp64")
+    lam, X, ref_hist = S.lobpcg(w.tree, otn, X0, n_iter, shift=lambda l: np.min(l) - 100.0,
+                                minres_tol=0.0)
+    for it in range(n_iter + 1):
+        assert _rel(hist[it], ref_hist[it]) <= 1e-10, it
+
+
+def test_lobpcg_fp32_within_a_tenth_of_a_wavenumber(T, ctx):
+    w, th, H = _c1(T, ctx)
+    otn = N.build_ttno(w.tree, w.ham)
+    blk = w.block()
+    X0 = _states(blk, w.n_states)
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    hist = T.ttn_lobpcg(ctx, H, bX, 3, -100.0, minres_tol=0.0, prec="fp32")
+    _, _, ref_hist = S.lobpcg(w.tree, otn, X0, 3, shift=lambda l: np.min(l) - 100.0,
+                              minres_tol=0.0)
+    err = np.abs(hist[-1] - ref_hist[-1])
+    assert err.max() <= 0.1, err            # cm^-1, per state
+
+
+def test_lobpcg_full_bond_reaches_exact_diagonalisation(T, ctx):
+    w, th, H = _c1(T, ctx, D=36)
+    ev = np.linalg.eigvalsh(N.dense_hamiltonian(w.ham))[:w.n_states]
+    blk = w.block()
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    hist = T.ttn_lobpcg(ctx, H, bX, 30, -100.0, als_sweeps=2, minres_max=40, minres_tol=1e-10,
+                        prec="fp64")
+    err = np.abs(hist - ev[None, :]) / abs(ev[0])
+    assert np.all(hist[1:] >= ev[None, :] - 1e-10 * abs(ev[0]))       # variational
+    assert err[-1].max() <= 1e-10, err[-1]
+
+
+def test_lobpcg_truncated_bond_is_variational_and_monotone(T, ctx):
+    w, th, H = _c1(T, ctx, D=8)
+    ev = np.linalg.eigvalsh(N.dense_hamiltonian(w.ham))[:w.n_states]
+    bX = T.block_from_arrays(ctx, th, w.bonds, w.block())
+    hist = T.ttn_lobpcg(ctx, H, bX, 8, -100.0, prec="fp64")
+    assert np.all(hist[1:] >= ev[None, :] - 1e-10 * abs(ev[0]))
+    assert np.all(np.diff(hist[1:], axis=0) <= 1e-9 * abs(ev[0]))
