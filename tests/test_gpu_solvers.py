@@ -113,7 +113,9 @@ def test_als_matches_oracle(T, ctx, prec):
     bR = T.block_from_arrays(ctx, th, w.bonds, blk)
     bY = T.block_from_arrays(ctx, th, w.bonds, blk)
     lam0 = N.expectation(w.tree, otn, X[0], X[0]) / N.overlap(w.tree, X[0], X[0])
-    shifts = lam0 - 100.0 + 10.0 * np.arange(w.n_states)
+    # shifts well below the spectrum keep H_eff - s well conditioned (the comparison then tests
+    # the implementation, not the rounding amplification of a near-singular local system)
+    shifts = lam0 - 300.0 - 10.0 * np.arange(w.n_states)
     T.ttn_als_solve(ctx, H, shifts, bR, bY, n_sweeps=2, minres_max=10, minres_tol=0.0, prec=prec)
     shp = [I.node_shape(w.tree, w.bonds, t) for t in range(w.tree.n_nodes)]
     got = T.block_to_arrays(bY, shp)
