@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--workload", default="c2")
+    ap.add_argument("--mode", default="lobpcg", choices=["lobpcg", "gram"],
+                    help="lobpcg: a step is one block-LOBPCG iteration (the headline); gram: a "
+                         "step is one 3n-state Gram (H and S), for kernel profiling")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -137,14 +140,15 @@ def roofline_of(prof, precision):
     """Roofline of the kernel with the largest summed event time in the timed region."""
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    prof = {k: v for k, v in prof.items() if not k.startswith("phase:")}
     name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
     sec = rec["ms"] / 1e3
-    if name.startswith("gemm_f32") or name.startswith("householder_qr_f32"):
+    if name.startswith(("gemm_f32", "level_f32", "closure_f32", "householder_qr_f32")):
         ach = rec["flops"] / sec / 1e12
         rl = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
-    elif name.startswith("gemm_f64") or name.startswith("householder_qr_f64") or \
-            name.startswith("jacobi"):
+    elif name.startswith(("gemm_f64", "level_f64", "closure_f64", "householder_qr_f64",
+                          "jacobi")):
         ach = rec["flops"] / sec / 1e12
         rl = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
               "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"}
@@ -187,6 +191,8 @@ def gpu_arm(args, rank, world, local, dist):
         T.ttn_block_copy_states(b, x0, list(range(n)))
         return b
 
+    if args.mode == "gram":
+        return gram_arm(args, T, ctx, th, H, w, stream, local, dist)
     # warm-up: W iterations on a copy
     xw = fresh()
     T.ttn_lobpcg(ctx, H, xw, args.warmup, SHIFT_OFFSET, **kw)
@@ -250,6 +256,37 @@ def gpu_arm(args, rank, world, local, dist):
             res[prec] = dict(ms=sec * 1e3, tflops=(T.ttn_flop_count(ctx) - f0) / sec / 1e12)
         out["gram"] = res
     return out
+
+
+def gram_arm(args, T, ctx, th, H, w, stream, local, dist):
+    """Step = <s_k|H|s_l> and <s_k|s_l> over the 3n-state subspace (the LOBPCG Gram)."""
+    import torch
+    from paper_2512_15875_gb300 import inputs as I
+    n = 3 * w.n_states
+    sblk = I.initial_block(w.tree, w.ham, w.bonds, n, seed=w.seed, noise=1e-2)
+    bS = T.block_from_arrays(ctx, th, w.bonds, sblk)
+    for _ in range(args.warmup):
+        T.ttn_gram(ctx, H, bS, bS, prec=args.precision)
+    T.ttn_synchronize(ctx)
+    launches0, flops0 = T.ttn_launch_count(ctx), T.ttn_flop_count(ctx)
+    T.ttn_profile_enable(ctx, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            T.ttn_gram(ctx, H, bS, bS, prec=args.precision)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3
+    prof = T.ttn_profile_get(ctx)
+    T.ttn_profile_enable(ctx, False)
+    return dict(t=t, n_conv=0, hist=np.zeros((2, 1)), prof=prof,
+                launches=T.ttn_launch_count(ctx) - launches0,
+                flops=T.ttn_flop_count(ctx) - flops0, clocks=clk.summary(), wbond=[0],
+                gram_mode=True)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -349,6 +386,19 @@ def main():
     if rank != 0:
         return
     w = workload(args.workload)
+    if out.get("gram_mode"):
+        rl = roofline_of(out["prof"], args.precision)
+        print(json.dumps({"mode": "gram", "metric": "Gram contraction TFLOP/s", "value":
+                          out["flops"] / t / 1e12, "unit": "TFLOP/s", "ms_per_step":
+                          t * 1e3 / args.steps, "steps": args.steps, "dtype": args.precision,
+                          "config": {"workload": f"{args.workload}: {w.description}",
+                                     "subspace": 3 * w.n_states},
+                          "roofline": rl, "clocks": out["clocks"],
+                          "gpu_launches": out["launches"],
+                          "kernels": {k: dict(v, share=v["ms"] / sum(x["ms"] for x in
+                                                                        out["prof"].values()))
+                                      for k, v in out["prof"].items()}}))
+        return
     value = n_conv / t
     rl = roofline_of(out["prof"], args.precision)
     line = {
@@ -369,6 +419,8 @@ def main():
         "roofline": rl,
         "clocks": out["clocks"],
         "gpu_launches": out["launches"],
+        "phases_ms_per_step": {k[6:]: v["ms"] / args.steps for k, v in out["prof"].items()
+                               if k.startswith("phase:")},
     }
     if "gram" in out:
         g = out["gram"]

@@ -270,7 +270,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.c_len = (long long)P * g.c_pstride;
     g.max_bra = ps.max_bra;
     g.max_ket = ps.max_ket;
-    launch_gemm<T>(ctx, g);
+    if (level_shape_ok(g)) launch_level<T>(ctx, g);
+    else launch_gemm<T>(ctx, g);
     prev_len = g.c_len;
     prev = Tl[l].p;
     prev_mode = MODE_PAIR;
@@ -345,7 +346,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.c_len = out_len;
     g.max_bra = ps.max_bra;
     g.max_ket = ps.max_ket;
-    launch_gemm<T>(ctx, g);
+    if (closure_shape_ok(g)) launch_closure<T>(ctx, g);
+    else launch_gemm<T>(ctx, g);
   } else if (out_kind == OUT_SCALAR) {
     TTN_REQUIRE(zsize == bra->size[t] && out_len >= P, "scalar closure: shape mismatch");
     launch_pair_dot<T>(ctx, block_node<T>(bra, t), bra->size[t], static_cast<const T*>(Z), zsize,

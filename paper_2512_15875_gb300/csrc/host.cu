@@ -511,16 +511,23 @@ static ttn_ttno* cached_identity(ttn_ctx* ctx, const TreeInfo& tree);
 // ------------------------------------------------------------------------------------------------
 // context
 // ------------------------------------------------------------------------------------------------
+// Identity TTNOs per context, released by ttn_destroy. The map itself is never destroyed: a
+// static destructor running after the CUDA runtime has been torn down at process exit must not
+// touch device memory.
 struct IdCache {
   std::vector<std::pair<TreeInfo, ttn_ttno*>> items;
-  ~IdCache() {
+  void release() {
     for (auto& it : items) delete it.second;
+    items.clear();
   }
 };
-static std::map<const ttn_ctx*, IdCache> g_id_cache;
+static std::map<const ttn_ctx*, IdCache>& id_caches() {
+  static auto* m = new std::map<const ttn_ctx*, IdCache>();
+  return *m;
+}
 
 static ttn_ttno* cached_identity(ttn_ctx* ctx, const TreeInfo& tree) {
-  IdCache& c = g_id_cache[ctx];
+  IdCache& c = id_caches()[ctx];
   for (auto& it : c.items)
     if (it.first.same_shape(tree)) return it.second;
   ttn_ttno* H = identity_ttno(ctx, tree);
@@ -566,7 +573,11 @@ void ttn_destroy(ttn_ctx* ctx) {
     return;
   }
   cudaStreamSynchronize(ctx->stream);
-  g_id_cache.erase(ctx);
+  auto it = id_caches().find(ctx);
+  if (it != id_caches().end()) {
+    it->second.release();
+    id_caches().erase(it);
+  }
   cudaStreamSynchronize(ctx->stream);
   for (auto& r : ctx->prof) {
     cudaEventDestroy(r.start);

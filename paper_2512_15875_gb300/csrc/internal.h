@@ -109,6 +109,14 @@ struct LaunchScope {
   ~LaunchScope();
 };
 
+// RAII helper for a driver phase ("phase:<name>"): events only, no launch counted.
+struct PhaseScope {
+  ttn_ctx* ctx;
+  int idx = -1;
+  PhaseScope(ttn_ctx* c, const char* name);
+  ~PhaseScope();
+};
+
 // ------------------------------------------------------------------------------------------------
 // TTNO
 // ------------------------------------------------------------------------------------------------
@@ -243,6 +251,12 @@ struct PairSet {
 };
 
 template <class T> void launch_gemm(ttn_ctx* ctx, const GemmDesc& g);
+// Specialised level-stage GEMM (one segment per item, a_sm = 1, N, K <= 64).
+bool level_shape_ok(const GemmDesc& g);
+template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
+// Specialised closure GEMM (one segment per item, a_sk = b_sk = 1, M, N <= 32).
+bool closure_shape_ok(const GemmDesc& g);
+template <class T> void launch_closure(ttn_ctx* ctx, const GemmDesc& g);
 
 // Operator stage of a node contraction (see engine.cu):
 //   Z[pair][slot][r][p] = sum_{g in slot} sum_q Tm[pair][prefix_g][q][r] * O_g[p][q]

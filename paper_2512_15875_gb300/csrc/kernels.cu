@@ -275,6 +275,26 @@ LaunchScope::~LaunchScope() {
   if (idx >= 0) cudaEventRecord(ctx->prof[idx].stop, ctx->stream);
 }
 
+PhaseScope::PhaseScope(ttn_ctx* c, const char* name) : ctx(c) {
+  if (!ctx->profiling) return;
+  const std::string full = std::string("phase:") + name;
+  int id = -1;
+  for (size_t i = 0; i < ctx->prof_names.size(); ++i)
+    if (ctx->prof_names[i] == full) id = (int)i;
+  if (id < 0) {
+    id = (int)ctx->prof_names.size();
+    ctx->prof_names.push_back(full);
+  }
+  LaunchRecord r{id, pool_event(ctx), pool_event(ctx), 0.0, 0.0};
+  CUDA_CHECK(cudaEventRecord(r.start, ctx->stream));
+  idx = (int)ctx->prof.size();
+  ctx->prof.push_back(r);
+}
+
+PhaseScope::~PhaseScope() {
+  if (idx >= 0) cudaEventRecord(ctx->prof[idx].stop, ctx->stream);
+}
+
 template <class T>
 void launch_gemm(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
@@ -476,6 +496,183 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
   }
   CUDA_LAUNCH_CHECK();
 }
+
+// Level stage of a node contraction, specialised for its shape: out[r][a] = sum_b in[b][r] E[a][b]
+// with rows r up to ~1e4 and a, b <= 64. One thread per row keeps all NA outputs in registers;
+// the environment slice is staged transposed (Es[b][a], zero-padded to NA) in shared memory and
+// read with broadcast vector loads; each item has exactly one segment.
+template <class T, int NA>
+__global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles) {
+  constexpr int KMAX = 64;
+  __shared__ __align__(16) T Es[KMAX * NA];
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const int seg = g.st.seg_ptr[sub];
+  const T* Ab = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
+  const T* Bb = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
+  for (int i = threadIdx.x; i < g.K * NA; i += kThreads) {
+    const int b = i / NA, a = i % NA;
+    Es[i] = a < g.N ? Bb[(long long)a * g.b_sn + (long long)b * g.b_sk] : T(0);
+  }
+  __syncthreads();
+  const int r = rt * kThreads + threadIdx.x;
+  if (r >= g.M) return;
+  T acc[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc[a] = T(0);
+  const T* src = Ab + r;
+  for (int b = 0; b < g.K; ++b) {
+    const T t = src[(long long)b * g.a_sk];
+    const T* e = Es + b * NA;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t, acc[a]);
+  }
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  T* dst = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] + (long long)r * g.c_sm;
+#pragma unroll
+  for (int a = 0; a < NA; ++a)
+    if (a < g.N) dst[a] = acc[a];
+}
+
+// True if the descriptor has the level-stage shape the specialised kernel handles.
+bool level_shape_ok(const GemmDesc& g) {
+  if (g.a_sm != 1 || g.c_sn != 1 || g.c_sm != g.N || g.K > 64 || g.N > 64) return false;
+  for (int s = 0; s < g.st.n_sub; ++s)
+    if (g.hst->seg_ptr[s + 1] - g.hst->seg_ptr[s] != 1) return false;
+  return true;
+}
+
+template <class T>
+void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
+  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
+  check_bounds(g, sizeof(T));
+  const int rtiles = (g.M + kThreads - 1) / kThreads;
+  const long long grid = (long long)rtiles * g.st.n_sub * g.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+  const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
+  const double bytes = (double)sizeof(T) * g.n_pairs * g.st.n_sub *
+                       ((double)g.M * g.N + (double)g.M * g.K + (double)g.N * g.K);
+  const int na = g.N <= 8 ? 8 : g.N <= 16 ? 16 : g.N <= 24 ? 24 : g.N <= 32 ? 32 : g.N <= 48 ? 48 : 64;
+  static const char* n64[] = {"level_f64_8", "level_f64_16", "level_f64_24", "level_f64_32",
+                              "level_f64_48", "level_f64_64"};
+  static const char* n32[] = {"level_f32_8", "level_f32_16", "level_f32_24", "level_f32_32",
+                              "level_f32_48", "level_f32_64"};
+  const int ci = na == 8 ? 0 : na == 16 ? 1 : na == 24 ? 2 : na == 32 ? 3 : na == 48 ? 4 : 5;
+  LaunchScope ls(ctx, sizeof(T) == 8 ? n64[ci] : n32[ci], flops, bytes);
+  cudaStream_t s = ctx->stream;
+  switch (na) {
+    case 8: level_kernel<T, 8><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 16: level_kernel<T, 16><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 24: level_kernel<T, 24><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 32: level_kernel<T, 32><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 48: level_kernel<T, 48><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    default: level_kernel<T, 64><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+  }
+  CUDA_LAUNCH_CHECK();
+}
+
+// Closure stage of a node contraction, specialised for its shape: C[a][b] = sum_k A[a][k] Z[b][k]
+// with a, b <= 32 and long k (A rows and Z rows contiguous in k). 256 threads = 4 groups that
+// take interleaved 32-wide k chunks; inside a group an 8 x 8 thread grid owns 4 x 4 output
+// tiles; shared tiles are k-major with a padded row (36) so 4-wide loads stay aligned; the four
+// partial sums are reduced through shared memory at the end.
+template <class T>
+__global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
+  constexpr int KC = sizeof(T) == 8 ? 16 : 32, LD = 36;
+  static_assert(2 * 4 * KC * LD >= 4096, "reduction buffer");
+  __shared__ __align__(16) T sh[2 * 4 * KC * LD];
+  T(*As)[KC][LD] = reinterpret_cast<T(*)[KC][LD]>(sh);
+  T(*Zs)[KC][LD] = reinterpret_cast<T(*)[KC][LD]>(sh + 4 * KC * LD);
+  const int sub = (int)(blockIdx.x % g.st.n_sub);
+  const int pair = (int)(blockIdx.x / g.st.n_sub);
+  const int seg = g.st.seg_ptr[sub];
+  const T* Ab = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
+  const T* Zb = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
+  const int grp = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int ty = t >> 3, tx = t & 7;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < g.K; k0 += 4 * KC) {
+    // each thread loads for every group: 4 x (32 x 32) A values and the same for Z
+    for (int i = threadIdx.x; i < 4 * KC * 32; i += kThreads) {
+      const int gg = i / (KC * 32), rem = i % (KC * 32);
+      const int row = rem / KC, kk = rem % KC;
+      const int k = k0 + gg * KC + kk;
+      As[gg][kk][row] = (row < g.M && k < g.K) ? Ab[(long long)row * g.a_sm + k] : T(0);
+      Zs[gg][kk][row] = (row < g.N && k < g.K) ? Zb[(long long)row * g.b_sn + k] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[grp][kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Zs[grp][kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  // reduce the four groups (reuse the tiles as [4][32][32])
+  T* red = sh;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[grp * 1024 + (ty * 4 + i) * 32 + tx * 4 + j] = acc[i][j];
+  __syncthreads();
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  T* Cb = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
+  for (int i = threadIdx.x; i < 1024; i += kThreads) {
+    const int a = i / 32, b = i % 32;
+    if (a < g.M && b < g.N)
+      Cb[(long long)a * g.c_sm + (long long)b * g.c_sn] =
+          red[i] + red[1024 + i] + red[2048 + i] + red[3072 + i];
+  }
+}
+
+bool closure_shape_ok(const GemmDesc& g) {
+  if (g.a_sk != 1 || g.b_sk != 1 || g.M > 32 || g.N > 32) return false;
+  for (int s = 0; s < g.st.n_sub; ++s)
+    if (g.hst->seg_ptr[s + 1] - g.hst->seg_ptr[s] != 1) return false;
+  return true;
+}
+
+template <class T>
+void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
+  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  TTN_REQUIRE(closure_shape_ok(g), "closure kernel: unsupported shape");
+  check_bounds(g, sizeof(T));
+  const long long grid = (long long)g.st.n_sub * g.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "closure grid too large");
+  const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
+  const double bytes = (double)sizeof(T) * g.n_pairs * g.st.n_sub *
+                       ((double)g.M * g.N + (double)(g.M + g.N) * g.K);
+  LaunchScope ls(ctx, sizeof(T) == 8 ? "closure_f64" : "closure_f32", flops, bytes);
+  closure_kernel<T><<<grid, kThreads, 0, ctx->stream>>>(g);
+  CUDA_LAUNCH_CHECK();
+}
+
+template void launch_closure<double>(ttn_ctx*, const GemmDesc&);
+template void launch_closure<float>(ttn_ctx*, const GemmDesc&);
+
+template void launch_level<double>(ttn_ctx*, const GemmDesc&);
+template void launch_level<float>(ttn_ctx*, const GemmDesc&);
 
 template void launch_op_stage<double>(ttn_ctx*, const OpStageDesc&);
 template void launch_op_stage<float>(ttn_ctx*, const OpStageDesc&);

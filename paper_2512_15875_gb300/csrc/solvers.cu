@@ -14,7 +14,11 @@
 #include <cstring>
 #include <numeric>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 ttn_ttno* identity_for(ttn_ctx* ctx, const TreeInfo& tree);
 template <class T>
@@ -427,6 +431,121 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
   }
 }
 
+// Cyclic Jacobi across the whole grid (cooperative launch; all CTAs resident). Each round of the
+// round-robin ordering rotates m/2 disjoint index pairs: phase 1 computes every pair's rotation
+// from the current A; phase 2 applies A <- J^T A J block by block (each 2 x 2 block (P, Q)
+// depends only on its own four entries and the rotations of P and Q) and V <- V J row by row.
+// The off-diagonal norm is reduced deterministically (per-CTA partials, summed in CTA order).
+struct JacobiArgs {
+  double* A;
+  double* V;
+  int m;
+  int max_sweeps;
+  double tol;
+  double* cs;       // [npairs]
+  double* sn;       // [npairs]
+  int* pp;          // [npairs]
+  int* qq;          // [npairs]
+  double* partial;  // [2 * gridDim.x]
+  int* done;        // [1]
+};
+
+__global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiArgs a) {
+  cg::grid_group grid = cg::this_grid();
+  const int m = a.m;
+  const int mp = m + (m & 1);
+  const int npairs = mp / 2;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  __shared__ double red[33];
+  for (long long idx = gtid; idx < (long long)m * m; idx += gstride)
+    a.V[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (long long idx = gtid; idx < (long long)m * m; idx += gstride) {
+      const double v = a.A[idx];
+      tot += v * v;
+      if (idx / m != idx % m) off += v * v;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (threadIdx.x == 0) {
+      a.partial[2 * blockIdx.x] = off;
+      a.partial[2 * blockIdx.x + 1] = tot;
+    }
+    grid.sync();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double so = 0.0, st = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        so += a.partial[2 * b];
+        st += a.partial[2 * b + 1];
+      }
+      a.done[0] = so <= a.tol * a.tol * st ? 1 : 0;
+    }
+    grid.sync();
+    if (a.done[0]) break;
+    for (int r = 0; r < mp - 1; ++r) {
+      for (long long i = gtid; i < npairs; i += gstride) {
+        int p, q;
+        if (i == 0) {
+          p = 0;
+          q = (r % (mp - 1)) + 1;
+        } else {
+          p = (int)((i + r) % (mp - 1)) + 1;
+          q = (int)((mp - 1 - i + r) % (mp - 1)) + 1;
+        }
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double c = 1.0, sv = 0.0;
+        if (q < m) {
+          const double apq = a.A[(long long)p * m + q];
+          if (apq != 0.0) {
+            const double theta = (a.A[(long long)q * m + q] - a.A[(long long)p * m + p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sv = t * c;
+          }
+        }
+        a.pp[i] = p;
+        a.qq[i] = q;
+        a.cs[i] = c;
+        a.sn[i] = sv;
+      }
+      grid.sync();
+      for (long long idx = gtid; idx < (long long)npairs * npairs; idx += gstride) {
+        const int P = (int)(idx / npairs), Q = (int)(idx % npairs);
+        const int p1 = a.pp[P], q1 = a.qq[P], p2 = a.pp[Q], q2 = a.qq[Q];
+        const double c1 = a.cs[P], s1 = a.sn[P], c2 = a.cs[Q], s2 = a.sn[Q];
+        const bool hq1 = q1 < m, hq2 = q2 < m;
+        const double x00 = a.A[(long long)p1 * m + p2];
+        const double x01 = hq2 ? a.A[(long long)p1 * m + q2] : 0.0;
+        const double x10 = hq1 ? a.A[(long long)q1 * m + p2] : 0.0;
+        const double x11 = (hq1 && hq2) ? a.A[(long long)q1 * m + q2] : 0.0;
+        // rows (J^T A), then columns (A J)
+        const double r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+        const double r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+        a.A[(long long)p1 * m + p2] = c2 * r00 - s2 * r01;
+        if (hq2) a.A[(long long)p1 * m + q2] = s2 * r00 + c2 * r01;
+        if (hq1) a.A[(long long)q1 * m + p2] = c2 * r10 - s2 * r11;
+        if (hq1 && hq2) a.A[(long long)q1 * m + q2] = s2 * r10 + c2 * r11;
+      }
+      for (long long idx = gtid; idx < (long long)m * npairs; idx += gstride) {
+        const int row = (int)(idx / npairs), Q = (int)(idx % npairs);
+        const int p2 = a.pp[Q], q2 = a.qq[Q];
+        if (q2 >= m) continue;
+        const double c2 = a.cs[Q], s2 = a.sn[Q];
+        const double vp = a.V[(long long)row * m + p2], vq = a.V[(long long)row * m + q2];
+        a.V[(long long)row * m + p2] = c2 * vp - s2 * vq;
+        a.V[(long long)row * m + q2] = s2 * vp + c2 * vq;
+      }
+      grid.sync();
+    }
+  }
+}
+
 // Sort eigenpairs ascending (stable in index), sign convention: the largest-|.| entry of each
 // eigenvector (first on ties) is positive. evals[i] = A[i][i]; Vout columns sorted.
 __global__ void sort_eig_kernel(const double* A, const double* V, int m, double* evals,
@@ -513,6 +632,47 @@ __global__ void symmetrize_kernel(double* A, int m) {
 // ------------------------------------------------------------------------------------------------
 // host-side drivers
 // ------------------------------------------------------------------------------------------------
+// Scratch (in doubles) of one grid Jacobi solve of size m: rotations, pairs, partial sums.
+static size_t jacobi_scratch_doubles(int m) {
+  const int np = (m + 1) / 2 + 1;
+  return (size_t)4 * np + 2 * 1024 + 8;
+}
+
+static int jacobi_grid_blocks(int device) {
+  static int cached[64] = {0};
+  if (device >= 0 && device < 64 && cached[device]) return cached[device];
+  int per_sm = 0, sms = 0;
+  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel, 256, 0));
+  CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  int b = std::max(1, std::min(per_sm, 2) * sms);
+  b = std::min(b, 1024);
+  if (device >= 0 && device < 64) cached[device] = b;
+  return b;
+}
+
+// Eigen-decomposition of the symmetric m x m matrix A (destroyed: diagonal = eigenvalues) with
+// eigenvectors in the columns of V, on the whole GPU. scratch: jacobi_scratch_doubles(m).
+static void launch_jacobi_grid(ttn_ctx* ctx, double* A, double* V, int m, double* scratch) {
+  const int np = (m + 1) / 2 + 1;
+  JacobiArgs a;
+  a.A = A;
+  a.V = V;
+  a.m = m;
+  a.max_sweeps = 40;
+  a.tol = 1e-15;
+  a.cs = scratch;
+  a.sn = scratch + np;
+  a.pp = reinterpret_cast<int*>(scratch + 2 * np);
+  a.qq = reinterpret_cast<int*>(scratch + 3 * np);
+  a.partial = scratch + 4 * np;
+  a.done = reinterpret_cast<int*>(scratch + 4 * np + 2 * 1024);
+  const int blocks = jacobi_grid_blocks(ctx->device);
+  void* args[] = {&a};
+  CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_grid_kernel, dim3(blocks), dim3(256),
+                                         args, 0, ctx->stream));
+}
+
+
 template <class T> T* work_node(ttn_block* b, int t);
 template <> double* work_node<double>(ttn_block* b, int t) {
   b->touch();
@@ -948,20 +1108,16 @@ static void rayleigh_ritz_device(ttn_ctx* ctx, int m, const double* dHt, const d
   const size_t mm = (size_t)m * m;
   DevBuf A(mm * sizeof(double), st), U(mm * sizeof(double), st), Us(mm * sizeof(double), st),
       mu(m * sizeof(double), st);
-  const int mp = m + (m & 1);
-  const size_t shj = (size_t)mp * sizeof(double) + (size_t)mp * sizeof(int) + 64;
+  DevBuf jac(jacobi_scratch_doubles(m) * sizeof(double), st);
   auto eig = [&](double* Ain, int k, double* evals, double* Vout) {
     {
       LaunchScope ls(ctx, "symmetrize", 0.0, 16.0 * k * k);
       symmetrize_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(Ain, k);
       CUDA_LAUNCH_CHECK();
     }
-    const int kp = k + (k & 1);
-    const size_t sh = (size_t)kp * sizeof(double) + (size_t)kp * sizeof(int) + 64;
     {
-      LaunchScope ls(ctx, "jacobi_f64", 0.0, 0.0);
-      jacobi_kernel<<<1, 1024, sh, st>>>(Ain, U.as<double>(), k, 40, 1e-15);
-      CUDA_LAUNCH_CHECK();
+      LaunchScope ls(ctx, "jacobi_grid_f64", 0.0, 0.0);
+      launch_jacobi_grid(ctx, Ain, U.as<double>(), k, jac.as<double>());
     }
     {
       LaunchScope ls(ctx, "sort_eig", 0.0, 0.0);
@@ -969,7 +1125,6 @@ static void rayleigh_ritz_device(ttn_ctx* ctx, int m, const double* dHt, const d
       CUDA_LAUNCH_CHECK();
     }
   };
-  (void)shj;
   CUDA_CHECK(cudaMemcpyAsync(A.p, dMt, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
   eig(A.as<double>(), m, mu.as<double>(), Us.as<double>());
   std::vector<double> hmu(m);
@@ -1075,6 +1230,7 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     const double s = *std::min_element(lam.begin(), lam.end()) + shift_offset;
     // residual r_j = H x_j - lambda_j x_j by fitting, starting from x_j
     {
+      PhaseScope ph(ctx, "residual_fit");
       std::vector<int> ids(n);
       std::iota(ids.begin(), ids.end(), 0);
       CUDA_CHECK(cudaStreamSynchronize(st));
@@ -1089,6 +1245,7 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     }
     // preconditioner: (H - s) y = r by ALS, starting from r
     {
+      PhaseScope ph(ctx, "als_precondition");
       std::vector<int> ids(n);
       std::iota(ids.begin(), ids.end(), 0);
       ttn_status cs = ttn_block_copy_states(Y.get(), R.get(), n, ids.data());
@@ -1122,11 +1279,20 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     DevBuf Ht((size_t)m * m * sizeof(double), st), Mt((size_t)m * m * sizeof(double), st);
     CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
     CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
-    gram_device(ctx, H, S.get(), S.get(), Ht.as<double>(), m, prec);
-    gram_device(ctx, Id, S.get(), S.get(), Mt.as<double>(), m, prec);
+    {
+      PhaseScope ph(ctx, "gram_H");
+      gram_device(ctx, H, S.get(), S.get(), Ht.as<double>(), m, prec);
+    }
+    {
+      PhaseScope ph(ctx, "gram_S");
+      gram_device(ctx, Id, S.get(), S.get(), Mt.as<double>(), m, prec);
+    }
     DevBuf th((size_t)n * sizeof(double), st), V((size_t)m * n * sizeof(double), st);
-    rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), n, rr_eps, th.as<double>(),
-                         V.as<double>());
+    {
+      PhaseScope ph(ctx, "rayleigh_ritz");
+      rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), n, rr_eps, th.as<double>(),
+                           V.as<double>());
+    }
     std::vector<double> hth(n), hV((size_t)m * n);
     CUDA_CHECK(cudaMemcpyAsync(hth.data(), th.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaMemcpyAsync(hV.data(), V.p, hV.size() * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1158,9 +1324,15 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
       std::vector<FitGroup> gs{g};
       fit_impl<T>(ctx, gs, out, fit_sweeps);
     };
-    fit_comb(Xn.get(), 0);
-    normalize_states<T>(ctx, Xn.get(), prec);
-    fit_comb(Pn.get(), n);
+    {
+      PhaseScope ph(ctx, "fit_x");
+      fit_comb(Xn.get(), 0);
+      normalize_states<T>(ctx, Xn.get(), prec);
+    }
+    {
+      PhaseScope ph(ctx, "fit_p");
+      fit_comb(Pn.get(), n);
+    }
     std::swap(P, Pn);
     have_p = true;
     {

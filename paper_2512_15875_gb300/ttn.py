@@ -6,8 +6,10 @@ library. There is no fallback: if the library is missing, every call raises.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -112,17 +114,37 @@ def _prec(p):
 # ----------------------------------------------------------------------------------------------
 # handles
 # ----------------------------------------------------------------------------------------------
+_LIVE = weakref.WeakValueDictionary()   # live handles, for an ordered release at exit
+_ORDER = {"ttn_envs_destroy": 0, "ttn_block_destroy": 1, "ttn_ttno_destroy": 2,
+          "ttn_tree_destroy": 3, "ttn_destroy": 4}
+
+
+def _release_all():
+    """Destroy every live handle before the interpreter (and the CUDA runtime) shuts down:
+    environments and blocks first, contexts last."""
+    for h in sorted(list(_LIVE.values()), key=lambda h: _ORDER.get(h._destroy, 9)):
+        try:
+            h.close()
+        except Exception:
+            pass
+
+
+atexit.register(_release_all)
+
+
 class _Handle:
     _destroy = None
 
     def __init__(self, ptr, ctx=None):
         self.ptr = ptr
         self.ctx = ctx
+        _LIVE[id(self)] = self
 
     def close(self):
         if self.ptr:
             getattr(load(), self._destroy)(self.ptr)
             self.ptr = None
+        _LIVE.pop(id(self), None)
 
     def __del__(self):
         try:
