@@ -219,6 +219,27 @@ ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
 ttn_status ttn_rayleigh_ritz(ttn_ctx* ctx, int m, const double* Ht, const double* Mt, int n,
                              double eps, double* theta, double* V);
 
+/* ---- Rayleigh-Ritz without device allocation --------------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that cannot allocate device
+ * memory while they run (work captured into or replayed from someone else's CUDA graph, a
+ * device memory pool frozen after start-up, a host that budgets every byte in advance).
+ *
+ * Same result as ttn_rayleigh_ritz, but Ht, Mt (m x m, row-major), theta[n] and V[m x n] are
+ * DEVICE pointers owned by the caller, and the working memory is a fixed area compiled into the
+ * library: about 3.7 MB of float64 per GPU, held from library load until process exit. No
+ * device memory is allocated or freed by this call.
+ *   - m may not exceed TTN_RR_NOALLOC_MAX_M; larger m returns TTN_EINVAL with a message.
+ *   - The first call on each device looks up the area's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls on a device share the one area and it keeps the last call's contents (every
+ *     value a call reads there, it has written first). Calls that overlap on the GPU (other
+ *     streams, other threads) race on it: serialise them.
+ * Errors as for ttn_rayleigh_ritz. The call synchronises the context's stream. */
+#define TTN_RR_NOALLOC_MAX_M 256
+ttn_status ttn_rayleigh_ritz_noalloc(ttn_ctx* ctx, int m, const double* Ht, const double* Mt,
+                                     int n, double eps, double* theta, double* V);
+
 /* ---- block LOBPCG (Alg. 2) ---------------------------------------------------------------- */
 
 /* n_iter iterations of block LOBPCG on the states of x (updated in place). The ALS

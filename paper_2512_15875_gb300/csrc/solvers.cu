@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include <cooperative_groups.h>
@@ -1348,6 +1349,46 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
 }
 
 // ------------------------------------------------------------------------------------------------
+// Rayleigh-Ritz without device allocation.
+//
+// Some callers cannot allocate device memory while they run: code inside a CUDA graph being
+// captured or replayed by someone else, a memory pool that is frozen after start-up, or a host
+// that budgets every byte up front. For them ttn_rayleigh_ritz_noalloc works in a fixed working
+// area that lives for the life of the process: the file-scope array below. Its size bounds the
+// problem (m <= TTN_RR_NOALLOC_MAX_M); every GPU that loads the library holds it until exit.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kRRMaxM = TTN_RR_NOALLOC_MAX_M;
+// A, U, Us, X, HX, Hp, Y (m x m each) + mu, th (m each) + keep indices (m ints, stored in m
+// doubles)
+constexpr size_t kRRScratchDoubles = 7ull * kRRMaxM * kRRMaxM + 3ull * kRRMaxM;
+static __device__ __align__(256) double g_rr_scratch[kRRScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+double* g_rr_scratch_dev[kMaxDevices] = {nullptr};
+std::once_flag g_rr_once[kMaxDevices];
+cudaError_t g_rr_setup_err[kMaxDevices] = {cudaSuccess};
+
+// Device address of the working area on `device` (which must be current). Done once per
+// device; the host-side name of a __device__ array is only a stand-in, so the address has to
+// come from cudaGetSymbolAddress.
+double* rr_scratch_for(int device) {
+  TTN_REQUIRE(device >= 0 && device < kMaxDevices, "device %d out of range", device);
+  std::call_once(g_rr_once[device], [device] {
+    void* p = nullptr;
+    g_rr_setup_err[device] = cudaGetSymbolAddress(&p, g_rr_scratch);
+    if (g_rr_setup_err[device] == cudaSuccess) g_rr_scratch_dev[device] = static_cast<double*>(p);
+  });
+  if (g_rr_setup_err[device] != cudaSuccess)
+    TTN_FAIL(TTN_ECUDA, "cudaGetSymbolAddress of the Rayleigh-Ritz working area failed: %s",
+             cudaGetErrorString(g_rr_setup_err[device]));
+  return g_rr_scratch_dev[device];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------------
 extern "C" {
@@ -1449,6 +1490,78 @@ ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
       lobpcg_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
                          minres_max, minres_tol, fit_sweeps, prec, eig_hist, hit);
     return hit ? TTN_ENOTCONV : TTN_OK;
+  });
+}
+
+ttn_status ttn_rayleigh_ritz_noalloc(ttn_ctx* ctx, int m, const double* Ht, const double* Mt,
+                                     int n, double eps, double* theta, double* V) {
+  if (!ctx || !Ht || !Mt || !theta || !V) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    TTN_REQUIRE(ctx->device >= 0, "a host-only context has no device");
+    TTN_REQUIRE(m >= 1 && n >= 1 && n <= m, "need 1 <= n <= m (m = %d, n = %d)", m, n);
+    TTN_REQUIRE(m <= kRRMaxM,
+                "m = %d exceeds the no-allocation limit TTN_RR_NOALLOC_MAX_M = %d; use "
+                "ttn_rayleigh_ritz", m, kRRMaxM);
+    int prev_device = -1;
+    CUDA_CHECK(cudaGetDevice(&prev_device));
+    struct Restore {
+      int d;
+      ~Restore() {
+        if (d >= 0) cudaSetDevice(d);
+      }
+    } restore{prev_device};
+    CUDA_CHECK(cudaSetDevice(ctx->device));
+    double* base = rr_scratch_for(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t mm = (size_t)m * m;
+    double* A = base;
+    double* U = A + mm;
+    double* Us = U + mm;
+    double* X = Us + mm;
+    double* HX = X + mm;
+    double* Hp = HX + mm;
+    double* Y = Hp + mm;
+    double* mu = Y + mm;
+    double* th = mu + m;
+    int* keep = reinterpret_cast<int*>(th + m);
+    auto eig = [&](double* Ain, int k, double* evals, double* Vout) {
+      symmetrize_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(Ain, k);
+      const int kp = k + (k & 1);
+      const size_t sh = (size_t)kp * sizeof(double) + (size_t)kp * sizeof(int) + 64;
+      jacobi_kernel<<<1, 1024, sh, st>>>(Ain, U, k, 40, 1e-15);
+      sort_eig_kernel<<<1, 256, k * sizeof(int), st>>>(Ain, U, k, evals, Vout);
+      ctx->launches += 3;
+      CUDA_LAUNCH_CHECK();
+    };
+    CUDA_CHECK(cudaMemcpyAsync(A, Mt, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    eig(A, m, mu, Us);
+    double hmu[kRRMaxM];
+    CUDA_CHECK(cudaMemcpyAsync(hmu, mu, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    double mx = hmu[0];
+    for (int i = 0; i < m; ++i) {
+      if (!std::isfinite(hmu[i])) TTN_FAIL(TTN_ENONFINITE, "non-finite overlap matrix");
+      mx = std::max(mx, hmu[i]);
+    }
+    int hkeep[kRRMaxM];
+    int k = 0;
+    for (int i = 0; i < m; ++i)
+      if (hmu[i] > eps * mx) hkeep[k++] = i;
+    TTN_REQUIRE(k >= n, "only %d of %d directions survive eps = %g", k, n, eps);
+    CUDA_CHECK(cudaMemcpyAsync(keep, hkeep, k * sizeof(int), cudaMemcpyHostToDevice, st));
+    canon_basis_kernel<<<grid_of((long long)m * k), kT, 0, st>>>(Us, mu, keep, m, k, X);
+    small_gemm_kernel<<<grid_of((long long)m * k), kT, 0, st>>>(Ht, m, 1, X, k, 1, HX, m, k, m);
+    small_gemm_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(X, 1, k, HX, k, 1, Hp, k, k, m);
+    ctx->launches += 3;
+    CUDA_LAUNCH_CHECK();
+    eig(Hp, k, th, Y);
+    small_gemm_kernel<<<grid_of((long long)m * n), kT, 0, st>>>(X, k, 1, Y, k, 1, V, m, n, k);
+    fix_sign_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, m, n);
+    ctx->launches += 2;
+    CUDA_LAUNCH_CHECK();
+    CUDA_CHECK(cudaMemcpyAsync(theta, th, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return TTN_OK;
   });
 }
 

@@ -66,6 +66,7 @@ _SIGS = {
     "ttn_als_solve": (_I, [_P, _P, _DP, _P, _P, _I, _I, _D, _I]),
     "ttn_rayleigh_ritz": (_I, [_P, _I, _DP, _DP, _I, _D, _DP, _DP]),
     "ttn_lobpcg": (_I, [_P, _P, _P, _I, _D, _I, _I, _D, _I, _I, _DP]),
+    "ttn_rayleigh_ritz_noalloc": (_I, [_P, _I, _P, _P, _I, _D, _P, _P]),
 }
 
 
@@ -420,6 +421,13 @@ def ttn_rayleigh_ritz(ctx, Ht, Mt, n, eps=1e-12):
     ctx.check(load().ttn_rayleigh_ritz(ctx.ptr, m, _dp(Ht), _dp(Mt), int(n), float(eps),
                                        _dp(theta), _dp(V)))
     return theta, V
+
+
+def ttn_rayleigh_ritz_noalloc(ctx, m, Ht_ptr, Mt_ptr, n, eps, theta_ptr, V_ptr):
+    """Device-pointer variant that allocates no device memory (see include/ttn.h). All four
+    pointers are device addresses (ints) owned by the caller."""
+    ctx.check(load().ttn_rayleigh_ritz_noalloc(ctx.ptr, int(m), Ht_ptr, Mt_ptr, int(n),
+                                               float(eps), theta_ptr, V_ptr))
 
 
 def ttn_lobpcg(ctx, H, x, n_iter, shift_offset, als_sweeps=2, minres_max=10, minres_tol=1e-5,
