@@ -46,14 +46,28 @@ NodePlan& get_plan(ttn_ttno* H, int t, int open) {
   };
   std::vector<G> groups;
   std::map<std::pair<int, int>, int> gidx;
+  struct FG {
+    int prefix, slot;
+    std::map<int, double> terms;   // w of the last contracted leg -> summed coefficient
+  };
+  std::vector<FG> fgs;
+  std::map<std::pair<int, int>, int> fidx;
   for (const TtnoEntry& e : H->entries[t]) {
     std::vector<int> key;
-    int par = 0;
+    int par = 0, par_prev = 0;
     for (int l = 0; l < mC; ++l) {
       key.push_back(e.w[p.C[l]]);
       auto ins = pref[l + 1].emplace(key, (int)pref[l + 1].size());
       if (ins.second) p.level[l].push_back({par, e.w[p.C[l]]});
+      par_prev = par;
       par = ins.first->second;
+    }
+    if (d == 1 && mC >= 1) {
+      const int slot_f = open >= 0 ? e.w[open] : 0;
+      auto fi = fidx.emplace(std::make_pair(par_prev, slot_f), (int)fgs.size());
+      if (fi.second) fgs.push_back({par_prev, slot_f, {}});
+      fgs[fi.first->second].terms[e.w[p.C[mC - 1]]] +=
+          e.coef * H->op_data[H->op_off[e.op]];
     }
     const int slot = open >= 0 ? e.w[open] : 0;
     auto gi = gidx.emplace(std::make_pair(par, slot), (int)groups.size());
@@ -72,6 +86,40 @@ NodePlan& get_plan(ttn_ttno* H, int t, int open) {
   }
   for (int s = 0; s < p.n_slots; ++s) p.slot_ptr[s + 1] += p.slot_ptr[s];
   cudaStream_t st = H->ctx->stream;
+  if (d == 1 && mC >= 1) {
+    p.fused = true;
+    std::stable_sort(fgs.begin(), fgs.end(),
+                     [](const FG& a, const FG& b) { return a.slot < b.slot; });
+    p.fG_slot_ptr.assign(p.n_slots + 1, 0);
+    p.fG_term_ptr.assign(1, 0);
+    for (const FG& g : fgs) {
+      p.fG_prefix.push_back(g.prefix);
+      p.fG_slot_ptr[g.slot + 1]++;
+      for (auto& kv : g.terms) {
+        p.fT_w.push_back(kv.first);
+        p.fT_coef.push_back(kv.second);
+      }
+      p.fG_term_ptr.push_back((int)p.fT_w.size());
+    }
+    for (int s2 = 0; s2 < p.n_slots; ++s2) p.fG_slot_ptr[s2 + 1] += p.fG_slot_ptr[s2];
+    const size_t nt = std::max<size_t>(p.fT_w.size(), 1);
+    p.d_fG_term_ptr = DevBuf(p.fG_term_ptr.size() * sizeof(int), st);
+    p.d_fT_w = DevBuf(nt * sizeof(int), st);
+    p.d_fT_coef64 = DevBuf(nt * sizeof(double), st);
+    p.d_fT_coef32 = DevBuf(nt * sizeof(float), st);
+    std::vector<float> c32(p.fT_coef.begin(), p.fT_coef.end());
+    CUDA_CHECK(cudaMemcpyAsync(p.d_fG_term_ptr.p, p.fG_term_ptr.data(),
+                               p.fG_term_ptr.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!p.fT_w.empty()) {
+      CUDA_CHECK(cudaMemcpyAsync(p.d_fT_w.p, p.fT_w.data(), p.fT_w.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, st));
+      CUDA_CHECK(cudaMemcpyAsync(p.d_fT_coef64.p, p.fT_coef.data(),
+                                 p.fT_coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+      CUDA_CHECK(cudaMemcpyAsync(p.d_fT_coef32.p, c32.data(), c32.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, st));
+    }
+    CUDA_CHECK(cudaStreamSynchronize(st));
+  }
   const size_t no = std::max<size_t>(p.ocomb.size(), 1);
   p.d_ocomb64 = DevBuf(no * sizeof(double), st);
   p.d_ocomb32 = DevBuf(no * sizeof(float), st);
@@ -119,7 +167,8 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
 
   using HostStage = StageHost;
   std::vector<HostStage> hs;
-  for (int l = 1; l <= mC; ++l) {
+  const int n_level_stages = p.fused ? mC - 1 : mC;
+  for (int l = 1; l <= n_level_stages; ++l) {
     HostStage s;
     const int c = p.C[l - 1];
     const long long eslice = (long long)Da[c] * Db[c];
@@ -132,7 +181,22 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
     }
     hs.push_back(std::move(s));
   }
-  {
+  if (p.fused) {
+    // segmented last level: Z[slot] = sum_{G in slot} T_{m-1}[prefix(G)] x Et[G]
+    HostStage s;
+    const int c = p.C[mC - 1];
+    const long long eslice = (long long)Da[c] * Db[c];
+    const long long zsize = sizes[mC];
+    for (int slot = 0; slot < p.n_slots; ++slot) {
+      for (int G = p.fG_slot_ptr[slot]; G < p.fG_slot_ptr[slot + 1]; ++G) {
+        s.seg_a.push_back(mC == 1 ? 0 : (long long)p.fG_prefix[G] * sizes[mC - 1]);
+        s.seg_b.push_back((long long)G * eslice);
+      }
+      s.seg_ptr.push_back((int)s.seg_a.size());
+      s.sub_c.push_back((long long)slot * zsize);
+    }
+    hs.push_back(std::move(s));
+  } else {
     HostStage s;
     const long long zsize = sizes[mC];
     for (int slot = 0; slot < p.n_slots; ++slot) {
@@ -240,7 +304,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
   int prev_mode = MODE_KET;
   long long prev_pstride = ksize;
   std::vector<DevBuf> Tl(mC + 1);
-  for (int l = 1; l <= mC; ++l) {
+  const int n_levels = p.fused ? mC - 1 : mC;
+  for (int l = 1; l <= n_levels; ++l) {
     const int c = p.C[l - 1];
     const long long rest = sizes[l - 1] / Db[c];
     const int nsub = (int)p.level[l - 1].size();
@@ -286,7 +351,48 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     zbuf = DevBuf((size_t)P * p.n_slots * zsize * sizeof(T), st);
     Z = zbuf.p;
   }
-  {
+  const long long z_len = out_kind == OUT_LOCAL ? out_len : (long long)P * p.n_slots * zsize;
+  if (p.fused) {
+    // fold the TTNO into the last contracted leg's environment, then one segmented level stage
+    const int c = p.C[mC - 1];
+    const int nG = (int)p.fG_prefix.size();
+    const long long eslice = (long long)Da[c] * Db[c];
+    DevBuf Et((size_t)std::max<long long>((long long)P * nG * eslice, 1) * sizeof(T), st);
+    int max_w = 0;
+    for (int x : p.fT_w) max_w = std::max(max_w, x);
+    const void* coef = sizeof(T) == 8 ? p.d_fT_coef64.p : p.d_fT_coef32.p;
+    launch_combine_env<T>(ctx, env[c], (long long)Dw[c] * eslice, eslice, Et.as<T>(), P, nG,
+                          p.d_fG_term_ptr.as<int>(), p.d_fT_w.as<int>(),
+                          static_cast<const T*>(coef), max_w);
+    GemmDesc g{};
+    const long long rest = sizes[mC - 1] / Db[c];
+    g.M = (int)rest;
+    g.N = Da[c];
+    g.K = Db[c];
+    g.a_sm = 1;
+    g.a_sk = rest;
+    g.b_sn = Db[c];
+    g.b_sk = 1;
+    g.c_sm = Da[c];
+    g.c_sn = 1;
+    g.A = {prev, prev_mode, prev_pstride};
+    g.B = {Et.p, MODE_PAIR, (long long)nG * eslice};
+    g.C = Z;
+    g.c_mode = MODE_PAIR;
+    g.c_pstride = (long long)p.n_slots * zsize;
+    g.n_pairs = P;
+    g.pair_bra = d_pb;
+    g.pair_ket = d_pk;
+    g.st = tab.stages[mC - 1];
+    g.hst = &tab.host[mC - 1];
+    g.a_len = prev_len;
+    g.b_len = std::max<long long>((long long)P * nG * eslice, 1);
+    g.c_len = z_len;
+    g.max_bra = ps.max_bra;
+    g.max_ket = ps.max_ket;
+    if (level_shape_ok(g)) launch_level<T>(ctx, g);
+    else launch_gemm<T>(ctx, g);
+  } else {
     OpStageDesc o{};
     o.d = d;
     o.rows = (int)zrest;
@@ -303,7 +409,7 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     o.pair_bra = d_pb;
     o.pair_ket = d_pk;
     o.a_len = prev_len;
-    o.z_len = out_kind == OUT_LOCAL ? out_len : (long long)P * o.z_pstride;
+    o.z_len = z_len;
     o.max_ket = ps.max_ket;
     o.max_prefix = 0;
     for (int x : p.grp_prefix) o.max_prefix = std::max(o.max_prefix, x);
@@ -339,8 +445,9 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.n_pairs = P;
     g.pair_bra = d_pb;
     g.pair_ket = d_pk;
-    g.st = tab.stages[mC + 1];
-    g.hst = &tab.host[mC + 1];
+    const int cl = p.fused ? mC : mC + 1;   // index of the closure stage in the tables
+    g.st = tab.stages[cl];
+    g.hst = &tab.host[cl];
     g.a_len = (long long)bra->n_states * bsize;
     g.b_len = (long long)P * p.n_slots * zsize;
     g.c_len = out_len;

@@ -138,6 +138,17 @@ struct NodePlan {
   std::vector<int> slot_ptr;                           // CSR over slots
   std::vector<double> ocomb;                           // per group: d x d  sum_e c_e O_e
   DevBuf d_ocomb64, d_ocomb32;
+  // Operator-first variant for nodes without a physical leg (d = 1) and m >= 1 contracted
+  // legs: the TTNO is folded into the last contracted leg's environment,
+  //   Et[G][a][b] = sum_{entries e in G} c_e E_Cm[w_Cm(e)][a][b],  G = (prefix_{m-1}, slot),
+  // and Z[slot] = sum_{G in slot} T_{m-1}[prefix(G)] x_Cm Et[G] is one segmented level stage.
+  bool fused = false;
+  std::vector<int> fG_prefix;        // per G: prefix index at level m-1 (0 if m == 1)
+  std::vector<int> fG_slot_ptr;      // CSR over slots
+  std::vector<int> fG_term_ptr;      // CSR over G: terms
+  std::vector<int> fT_w;             // per term: w of the last contracted leg
+  std::vector<double> fT_coef;       // per term: coefficient (times the 1 x 1 operator)
+  DevBuf d_fG_term_ptr, d_fT_w, d_fT_coef64, d_fT_coef32;
 };
 
 // Item tables of one GEMM stage: per item ("sub") the C offset and a CSR list of segments,
@@ -251,7 +262,12 @@ struct PairSet {
 };
 
 template <class T> void launch_gemm(ttn_ctx* ctx, const GemmDesc& g);
-// Specialised level-stage GEMM (one segment per item, a_sm = 1, N, K <= 64).
+// Et[pair][G] = sum_{t in G} coef_t E[pair][w_t] (operator-first fold of a d = 1 node).
+template <class T>
+void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long eslice, T* Et,
+                        int n_pairs, int nG, const int* term_ptr, const int* term_w,
+                        const T* term_coef, int max_w);
+// Specialised level-stage GEMM (a_sm = 1, N, K <= 64; items sum over their segments).
 bool level_shape_ok(const GemmDesc& g);
 template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
 // Specialised closure GEMM (one segment per item, a_sk = b_sk = 1, M, N <= 32).

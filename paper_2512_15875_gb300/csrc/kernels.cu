@@ -397,6 +397,14 @@ void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* 
   CUDA_LAUNCH_CHECK();
 }
 
+// Groups per shared-memory chunk of the operator stage: up to 32 KB of d x d operators, at most
+// 512 groups (their prefix indices are staged too).
+template <class T, int D>
+__host__ __device__ constexpr int op_stage_chunk() {
+  constexpr int e = 8192 / (int)sizeof(T) * 4 / (D * D);
+  return e < 1 ? 1 : (e > 512 ? 512 : e);
+}
+
 // One thread per output row r of one (pair, slot); all d outputs of the row in registers.
 // The combined operators of the slot's groups are staged through shared memory in chunks;
 // the output tile is transposed through shared memory so the global stores are coalesced.
@@ -404,8 +412,7 @@ template <class T, int D>
 __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int rtiles) {
   extern __shared__ unsigned char sh_raw[];
   T* sh = reinterpret_cast<T*>(sh_raw);
-  constexpr int kOpElems = 8192 / sizeof(T) * 4;   // 32 KB of operators per chunk
-  constexpr int GCH = kOpElems / (D * D) > 0 ? kOpElems / (D * D) : 1;
+  constexpr int GCH = op_stage_chunk<T, D>();
   T* sop = sh;
   T* sout = sh + GCH * D * D;                        // kThreads x (D + 1)
   const long long bid = blockIdx.x;
@@ -425,14 +432,35 @@ __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int r
 #pragma unroll
   for (int p = 0; p < D; ++p) acc[p] = T(0);
   const int g0 = o.slot_ptr[slot], g1 = o.slot_ptr[slot + 1];
+  __shared__ int spre[GCH];
   for (int gc = g0; gc < g1; gc += GCH) {
     const int ng = min(GCH, g1 - gc);
     for (int i = threadIdx.x; i < ng * D * D; i += kThreads)
       sop[i] = ops[(long long)gc * D * D + i];
+    for (int i = threadIdx.x; i < ng; i += kThreads) spre[i] = o.grp_prefix[gc + i];
     __syncthreads();
     if (r < o.rows) {
-      for (int g = 0; g < ng; ++g) {
-        const T* src = Tb + (long long)o.grp_prefix[gc + g] * o.tsize + r;
+      int g = 0;
+      // two groups at a time for small d (independent loads in flight); large d would spill
+      for (; D <= 16 && g + 2 <= ng; g += 2) {
+        const T* s0 = Tb + (long long)spre[g] * o.tsize + r;
+        const T* s1 = Tb + (long long)spre[g + 1] * o.tsize + r;
+        T t0[D], t1[D];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          t0[q] = s0[(long long)q * o.rows];
+          t1[q] = s1[(long long)q * o.rows];
+        }
+        const T* O0 = sop + g * D * D;
+        const T* O1 = O0 + D * D;
+#pragma unroll
+        for (int q = 0; q < D; ++q)
+#pragma unroll
+          for (int p = 0; p < D; ++p)
+            acc[p] = fma(O1[p * D + q], t1[q], fma(O0[p * D + q], t0[q], acc[p]));
+      }
+      for (; g < ng; ++g) {
+        const T* src = Tb + (long long)spre[g] * o.tsize + r;
         const T* O = sop + g * D * D;
 #pragma unroll
         for (int q = 0; q < D; ++q) {
@@ -456,12 +484,14 @@ __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int r
 
 template <class T, int D>
 static void op_stage_dispatch(ttn_ctx* ctx, const OpStageDesc& o, int rtiles, long long grid) {
-  constexpr int kOpElems = 8192 / sizeof(T) * 4;
-  constexpr int GCH = kOpElems / (D * D) > 0 ? kOpElems / (D * D) : 1;
+  constexpr int GCH = op_stage_chunk<T, D>();
   const size_t shmem = sizeof(T) * ((size_t)GCH * D * D + (size_t)kThreads * (D + 1));
-  if (shmem > 48 * 1024)
+  static int set_for_device[64] = {0};
+  if (ctx->device >= 0 && ctx->device < 64 && !set_for_device[ctx->device]) {
     CUDA_CHECK(cudaFuncSetAttribute(op_stage_kernel<T, D>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
+    set_for_device[ctx->device] = 1;
+  }
   op_stage_kernel<T, D><<<grid, kThreads, shmem, ctx->stream>>>(o, rtiles);
 }
 
@@ -504,49 +534,124 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
 template <class T, int NA>
 __global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles) {
   constexpr int KMAX = 64;
+  // the output tile (kThreads rows x NA, rows contiguous in global memory) is staged through a
+  // padded shared buffer so the global stores are coalesced; only where it fits statically
+  constexpr bool kStage = sizeof(T) == 4 && NA <= 32;
+  constexpr int kOutLd = NA + 1;
   __shared__ __align__(16) T Es[KMAX * NA];
+  __shared__ T Os[kStage ? kThreads * kOutLd : 1];
   const long long bid = blockIdx.x;
   const int rt = (int)(bid % rtiles);
   const long long rest = bid / rtiles;
   const int sub = (int)(rest % g.st.n_sub);
   const int pair = (int)(rest / g.st.n_sub);
-  const int seg = g.st.seg_ptr[sub];
-  const T* Ab = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
-  const T* Bb = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
+  const T* Abase = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket);
+  const T* Bbase = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket);
+  const int r0 = rt * kThreads;
+  const int r = r0 + threadIdx.x;
+  const bool live = r < g.M;
+  T acc[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc[a] = T(0);
+  for (int seg = g.st.seg_ptr[sub]; seg < g.st.seg_ptr[sub + 1]; ++seg) {
+  const T* Ab = Abase + g.st.seg_a[seg];
+  const T* Bb = Bbase + g.st.seg_b[seg];
+  __syncthreads();
   for (int i = threadIdx.x; i < g.K * NA; i += kThreads) {
     const int b = i / NA, a = i % NA;
     Es[i] = a < g.N ? Bb[(long long)a * g.b_sn + (long long)b * g.b_sk] : T(0);
   }
   __syncthreads();
-  const int r = rt * kThreads + threadIdx.x;
-  if (r >= g.M) return;
-  T acc[NA];
+  if (live) {
+    const T* src = Ab + r;
+    int b = 0;
+    for (; b + 4 <= g.K; b += 4) {
+      T t[4];
 #pragma unroll
-  for (int a = 0; a < NA; ++a) acc[a] = T(0);
-  const T* src = Ab + r;
-  for (int b = 0; b < g.K; ++b) {
-    const T t = src[(long long)b * g.a_sk];
-    const T* e = Es + b * NA;
+      for (int u = 0; u < 4; ++u) t[u] = src[(long long)(b + u) * g.a_sk];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t, acc[a]);
+      for (int u = 0; u < 4; ++u) {
+        const T* e = Es + (b + u) * NA;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t[u], acc[a]);
+      }
+    }
+    for (; b < g.K; ++b) {
+      const T t = src[(long long)b * g.a_sk];
+      const T* e = Es + b * NA;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t, acc[a]);
+    }
+  }
   }
   long long cidx = 0;
   if (g.c_mode == MODE_PAIR) cidx = pair;
   else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
   else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
-  T* dst = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] + (long long)r * g.c_sm;
+  T* base = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
+  if constexpr (kStage) {
 #pragma unroll
-  for (int a = 0; a < NA; ++a)
-    if (a < g.N) dst[a] = acc[a];
+    for (int a = 0; a < NA; ++a) Os[threadIdx.x * kOutLd + a] = acc[a];
+    __syncthreads();
+    const int nrow = min(kThreads, g.M - r0);
+    T* dst = base + (long long)r0 * g.c_sm;     // c_sm == N: the tile is contiguous
+    for (int i = threadIdx.x; i < nrow * g.N; i += kThreads)
+      dst[i] = Os[(i / g.N) * kOutLd + (i % g.N)];
+  } else {
+    if (!live) return;
+    T* dst = base + (long long)r * g.c_sm;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+      if (a < g.N) dst[a] = acc[a];
+  }
 }
 
 // True if the descriptor has the level-stage shape the specialised kernel handles.
 bool level_shape_ok(const GemmDesc& g) {
-  if (g.a_sm != 1 || g.c_sn != 1 || g.c_sm != g.N || g.K > 64 || g.N > 64) return false;
-  for (int s = 0; s < g.st.n_sub; ++s)
-    if (g.hst->seg_ptr[s + 1] - g.hst->seg_ptr[s] != 1) return false;
-  return true;
+  return g.a_sm == 1 && g.c_sn == 1 && g.c_sm == g.N && g.K <= 64 && g.N <= 64;
 }
+
+template <class T>
+__global__ void combine_env_kernel(const T* __restrict__ E, long long e_pstride,
+                                   long long eslice, T* __restrict__ Et, int nG,
+                                   const int* __restrict__ term_ptr, const int* __restrict__ term_w,
+                                   const T* __restrict__ term_coef, long long total) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long per_pair = (long long)nG * eslice;
+    const long long pair = idx / per_pair;
+    const long long r = idx - pair * per_pair;
+    const int G = (int)(r / eslice);
+    const long long e = r - (long long)G * eslice;
+    const T* Ep = E + pair * e_pstride + e;
+    T acc = T(0);
+    for (int t = term_ptr[G]; t < term_ptr[G + 1]; ++t)
+      acc = fma(term_coef[t], Ep[(long long)term_w[t] * eslice], acc);
+    Et[idx] = acc;
+  }
+}
+
+template <class T>
+void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long eslice, T* Et,
+                        int n_pairs, int nG, const int* term_ptr, const int* term_w,
+                        const T* term_coef, int max_w) {
+  const long long total = (long long)n_pairs * nG * eslice;
+  if (total == 0) return;
+  TTN_REQUIRE((long long)(max_w + 1) * eslice <= e_pstride, "combine bounds");
+  LaunchScope ls(ctx, sizeof(T) == 8 ? "combine_env_f64" : "combine_env_f32", 2.0 * total,
+                 sizeof(T) * 2.0 * total);
+  long long blocks = (total + kThreads - 1) / kThreads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  combine_env_kernel<T><<<(int)blocks, kThreads, 0, ctx->stream>>>(E, e_pstride, eslice, Et, nG,
+                                                                 term_ptr, term_w, term_coef,
+                                                                 total);
+  CUDA_LAUNCH_CHECK();
+}
+
+template void launch_combine_env<double>(ttn_ctx*, const double*, long long, long long, double*,
+                                         int, int, const int*, const int*, const double*, int);
+template void launch_combine_env<float>(ttn_ctx*, const float*, long long, long long, float*,
+                                        int, int, const int*, const int*, const float*, int);
 
 template <class T>
 void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
@@ -556,9 +661,11 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   const int rtiles = (g.M + kThreads - 1) / kThreads;
   const long long grid = (long long)rtiles * g.st.n_sub * g.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
-  const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
-  const double bytes = (double)sizeof(T) * g.n_pairs * g.st.n_sub *
-                       ((double)g.M * g.N + (double)g.M * g.K + (double)g.N * g.K);
+  long long nseg = 0;
+  for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
+  const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
+  const double bytes = (double)sizeof(T) * g.n_pairs *
+                       ((double)g.M * g.N * g.st.n_sub + ((double)g.M * g.K + g.N * g.K) * nseg);
   const int na = g.N <= 8 ? 8 : g.N <= 16 ? 16 : g.N <= 24 ? 24 : g.N <= 32 ? 32 : g.N <= 48 ? 48 : 64;
   static const char* n64[] = {"level_f64_8", "level_f64_16", "level_f64_24", "level_f64_32",
                               "level_f64_48", "level_f64_64"};
@@ -576,6 +683,22 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     default: level_kernel<T, 64><<<grid, kThreads, 0, s>>>(g, rtiles); break;
   }
   CUDA_LAUNCH_CHECK();
+}
+
+__device__ __forceinline__ void load4(const float* p, float* v) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double* p, double* v) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  const double2 y = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = y.x;
+  v[3] = y.y;
 }
 
 // Closure stage of a node contraction, specialised for its shape: C[a][b] = sum_k A[a][k] Z[b][k]
@@ -615,10 +738,8 @@ __global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
 #pragma unroll 4
     for (int kk = 0; kk < KC; ++kk) {
       T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[grp][kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Zs[grp][kk][tx * 4 + j];
+      load4(&As[grp][kk][ty * 4], a);   // 16-byte aligned: row stride 36, offset 4*ty
+      load4(&Zs[grp][kk][tx * 4], b);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
