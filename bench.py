@@ -143,21 +143,26 @@ def roofline_of(prof, precision):
     prof = {k: v for k, v in prof.items() if not k.startswith("phase:")}
     name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
     sec = rec["ms"] / 1e3
-    if name.startswith(("gemm_f32", "level_f32", "closure_f32", "householder_qr_f32")):
-        ach = rec["flops"] / sec / 1e12
-        rl = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"}
-    elif name.startswith(("gemm_f64", "level_f64", "closure_f64", "householder_qr_f64",
-                          "jacobi")):
-        ach = rec["flops"] / sec / 1e12
-        rl = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-              "peak_source": "nominal GB300 FP64 1.25 TFLOP/s"}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = ("MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
+               else "fallback 6800 GB/s (of fallback)")
+    if "f64" in name or name.startswith("jacobi"):
+        alu, alu_src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 1.25 TFLOP/s"
     else:
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        ach = rec["bytes"] / sec / 1e9
-        rl = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks
-              else "fallback 6800 GB/s (of fallback)"}
+        alu, alu_src = FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"
+    # classic roofline: the kernel's algorithmic intensity against the machine balance decides
+    # which ceiling binds
+    intensity = rec["flops"] / max(rec["bytes"], 1.0)
+    balance = alu * 1e12 / (hbm * 1e9)
+    if rec["flops"] > 0 and intensity >= balance:
+        rl = {"bound": "alu", "achieved": rec["flops"] / sec / 1e12, "peak": alu,
+              "unit": "TFLOP/s", "peak_source": alu_src}
+    else:
+        rl = {"bound": "hbm", "achieved": rec["bytes"] / sec / 1e9, "peak": hbm, "unit": "GB/s",
+              "peak_source": hbm_src}
+    rl["intensity_flop_per_byte"] = intensity
+    rl["machine_balance_flop_per_byte"] = balance
+    rl["flops_rate_tflops"] = rec["flops"] / sec / 1e12
     rl["frac"] = rl["achieved"] / rl["peak"]
     rl["kernel"] = name
     rl["launches"] = rec["launches"]

@@ -16,6 +16,7 @@
 // kept block-sparse: only distinct (w-prefix) and (prefix, w_open) combinations are contracted.
 #include <algorithm>
 #include <cstring>
+#include <set>
 
 #include "internal.h"
 
@@ -413,6 +414,7 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     o.max_ket = ps.max_ket;
     o.max_prefix = 0;
     for (int x : p.grp_prefix) o.max_prefix = std::max(o.max_prefix, x);
+    o.n_unique_prefix = (int)std::set<int>(p.grp_prefix.begin(), p.grp_prefix.end()).size();
     launch_op_stage<T>(ctx, o);
   }
 

@@ -291,6 +291,7 @@ struct OpStageDesc {
   // host-side validation
   long long a_len, z_len;
   int max_ket, max_prefix;
+  int n_unique_prefix;      // distinct T_m slices read (algorithmic bytes)
 };
 template <class T> void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o);
 template <class T>

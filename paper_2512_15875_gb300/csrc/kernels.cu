@@ -1,6 +1,7 @@
 // Generic device kernels of the contraction engine: a strided batched GEMM with per-item
 // segment sums (the workhorse of every node contraction), tensor permutes, per-pair dots.
 #include <cstdio>
+#include <set>
 
 #include "internal.h"
 
@@ -209,6 +210,23 @@ int grid_for(long long n) {
 
 }  // namespace
 
+// Algorithmic bytes of a strided batched launch: every distinct A and B slice read once per
+// distinct base (pair / bra / ket index), every output item written once.
+static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
+  std::set<long long> ua(g.hst->seg_a.begin(), g.hst->seg_a.end());
+  std::set<long long> ub(g.hst->seg_b.begin(), g.hst->seg_b.end());
+  auto bases = [&](int mode) -> double {
+    if (mode == MODE_PAIR) return g.n_pairs;
+    if (mode == MODE_BRA) return std::min(g.n_pairs, g.max_bra + 1);
+    if (mode == MODE_KET) return std::min(g.n_pairs, g.max_ket + 1);
+    return 1.0;
+  };
+  const double a = bases(g.A.mode) * (double)ua.size() * g.M * g.K;
+  const double b = bases(g.B.mode) * (double)ub.size() * g.N * g.K;
+  const double c = (double)g.n_pairs * g.st.n_sub * g.M * g.N;
+  return (double)elem * (a + b + c);
+}
+
 // Host-side proof that every address the launch can form lies inside its buffer: for each item
 // and segment, the smallest and largest offsets over (m, n, k) and over all pairs.
 static void check_bounds(const GemmDesc& g, size_t elem) {
@@ -321,8 +339,7 @@ void launch_gemm(ttn_ctx* ctx, const GemmDesc& g) {
   static const char* names32[] = {"gemm_f32_64x64", "gemm_f32_64x32", "gemm_f32_32x32",
                                   "gemm_f32_128x16", "gemm_f32_64x16", "gemm_f32_16x16"};
   const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
-  const double bytes = (double)sizeof(T) * g.n_pairs *
-                       ((double)g.M * g.N * g.st.n_sub + (double)(g.M + g.N) * g.K * nseg);
+  const double bytes = algorithmic_bytes(g, sizeof(T));
   LaunchScope ls(ctx, sizeof(T) == 8 ? names64[best] : names32[best], flops, bytes);
   dispatch<T>(best, g, tm, tn, grid, ctx->stream);
   CUDA_LAUNCH_CHECK();
@@ -513,7 +530,7 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
   TTN_REQUIRE(grid <= 0x7fffffffLL, "op stage grid too large");
   const double flops = 2.0 * o.d * o.d * (double)o.rows * o.n_groups * o.n_pairs;
   const double bytes = (double)sizeof(T) * o.n_pairs *
-                       ((double)o.n_groups * o.tsize + (double)o.n_slots * o.rows * o.d);
+                       ((double)o.n_unique_prefix * o.tsize + (double)o.n_slots * o.rows * o.d);
   LaunchScope ls(ctx, sizeof(T) == 8 ? "op_stage_f64" : "op_stage_f32", flops, bytes);
   switch (o.d) {
 #define TTN_OPD(k) case k: op_stage_dispatch<T, k>(ctx, o, rtiles, grid); break;
@@ -664,8 +681,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   long long nseg = 0;
   for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
   const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
-  const double bytes = (double)sizeof(T) * g.n_pairs *
-                       ((double)g.M * g.N * g.st.n_sub + ((double)g.M * g.K + g.N * g.K) * nseg);
+  const double bytes = algorithmic_bytes(g, sizeof(T));
   const int na = g.N <= 8 ? 8 : g.N <= 16 ? 16 : g.N <= 24 ? 24 : g.N <= 32 ? 32 : g.N <= 48 ? 48 : 64;
   static const char* n64[] = {"level_f64_8", "level_f64_16", "level_f64_24", "level_f64_32",
                               "level_f64_48", "level_f64_64"};
@@ -782,8 +798,7 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
   const long long grid = (long long)g.st.n_sub * g.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "closure grid too large");
   const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
-  const double bytes = (double)sizeof(T) * g.n_pairs * g.st.n_sub *
-                       ((double)g.M * g.N + (double)(g.M + g.N) * g.K);
+  const double bytes = algorithmic_bytes(g, sizeof(T));
   LaunchScope ls(ctx, sizeof(T) == 8 ? "closure_f64" : "closure_f32", flops, bytes);
   closure_kernel<T><<<grid, kThreads, 0, ctx->stream>>>(g);
   CUDA_LAUNCH_CHECK();
