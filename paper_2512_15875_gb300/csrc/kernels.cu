@@ -582,12 +582,12 @@ __global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles)
   if (live) {
     const T* src = Ab + r;
     int b = 0;
-    for (; b + 4 <= g.K; b += 4) {
-      T t[4];
+    for (; b + 8 <= g.K; b += 8) {
+      T t[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) t[u] = src[(long long)(b + u) * g.a_sk];
+      for (int u = 0; u < 8; ++u) t[u] = src[(long long)(b + u) * g.a_sk];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const T* e = Es + (b + u) * NA;
 #pragma unroll
         for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t[u], acc[a]);
