@@ -219,6 +219,22 @@ ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
 ttn_status ttn_rayleigh_ritz(ttn_ctx* ctx, int m, const double* Ht, const double* Mt, int n,
                              double eps, double* theta, double* V);
 
+/* ---- block inverse iteration (Alg. 3, Eq. inverse iteration update) ----------------------- */
+
+/* n_iter iterations of block inverse iteration on the states of x (updated in place). The
+ * current Rayleigh quotients are grouped by single linkage: sorted values closer than
+ * cluster_gap form one block (Sec. III.B uses 5 cm^-1); cluster_gap <= 0 gives one block per
+ * state (a shift per state). Each block's shift is the mean Rayleigh quotient of its states;
+ * every state solves (H - shift) y = x by ALS (als_sweeps sweeps, MINRES <= minres_max,
+ * relative tolerance minres_tol) and is normalised; a block of more than one state is
+ * re-orthogonalised by its own Rayleigh-Ritz step and refitted (fit_sweeps). rq_hist
+ * [(n_iter+1) x n] receives the values after each iteration (row 0 = initial quotients).
+ * Returns TTN_ENOTCONV (results written) if a local solve hit its cap. */
+ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
+                                 double cluster_gap, int als_sweeps, int minres_max,
+                                 double minres_tol, int fit_sweeps, ttn_precision prec,
+                                 double* rq_hist);
+
 /* ---- Rayleigh-Ritz without device allocation --------------------------------------------- */
 
 /* The paper has no counterpart to this call; it serves callers that cannot allocate device

@@ -254,28 +254,50 @@ def lobpcg(tree, ttno, X0, n_iter, shift, als_sweeps=2, minres_max=10, minres_to
     return lam, X, hist
 
 
-def inverse_iteration(tree, ttno, X0, n_iter, shifts, als_sweeps=1, minres_max=10000,
-                      minres_tol=1e-5):
-    """Block inverse iteration (Alg. 3, Eq. inverse iteration update) with one shift per state
-    (``shifts`` is a function of the current Rayleigh quotients), followed in every iteration by
-    the Rayleigh-Ritz step over the block."""
+def clusters_by_gap(lam, gap):
+    """Single-linkage clusters of the Rayleigh quotients: sorted values closer than ``gap`` join
+    (Sec. III.B: states whose Rayleigh quotients differ by less than 5 cm^-1 form one block)."""
+    order = [int(i) for i in np.argsort(lam, kind="stable")]
+    out = [[order[0]]]
+    for a, b in zip(order[:-1], order[1:]):
+        if lam[b] - lam[a] < gap:
+            out[-1].append(b)
+        else:
+            out.append([b])
+    return [sorted(c) for c in out]
+
+
+def inverse_iteration(tree, ttno, X0, n_iter, clusters, als_sweeps=1, minres_max=10000,
+                      minres_tol=1e-5, fit_sweeps=2):
+    """Block inverse iteration (Alg. 3, Eq. inverse iteration update). ``clusters`` maps the
+    current Rayleigh quotients to a list of blocks (lists of state indices); each block uses the
+    mean Rayleigh quotient of its states as the shift, every state is solved by ALS, and a block
+    of more than one state is re-orthogonalised by its own Rayleigh-Ritz step.
+    Returns (Rayleigh quotients, states, per-iteration values)."""
+    idt = identity_ttno(tree)
     n = len(X0)
     X = [normalize(tree, x) for x in X0]
     lam = np.array([expectation(tree, ttno, x, x) for x in X])
+    hist = [lam.copy()]
     for _ in range(n_iter):
-        s = shifts(lam)
-        Y = [normalize(tree, als_solve(tree, ttno, s[j], X[j], X[j], als_sweeps, minres_max,
+        blocks = clusters(lam)
+        shift = np.zeros(n)
+        for c in blocks:
+            shift[c] = np.mean(lam[c])
+        Y = [normalize(tree, als_solve(tree, ttno, shift[j], X[j], X[j], als_sweeps, minres_max,
                                        minres_tol)) for j in range(n)]
-        if n > 1:
-            Ht, Mt = gram_block(tree, ttno, Y)
-            theta, V = rayleigh_ritz(Ht, Mt, n)
-            idt = identity_ttno(tree)
-            X = []
-            for j in range(n):
-                tx = [(V[k, j], idt, Y[k]) for k in range(n)]
-                X.append(normalize(tree, fit(tree, tx, fit_initial(tx), 2)))
-            lam = theta
-        else:
-            X = Y
-            lam = np.array([expectation(tree, ttno, X[0], X[0])])
-    return lam, X
+        Xn, lam_n = list(Y), lam.copy()
+        for c in blocks:
+            if len(c) == 1:
+                j = c[0]
+                lam_n[j] = expectation(tree, ttno, Y[j], Y[j])
+                continue
+            Ht, Mt = gram_block(tree, ttno, [Y[j] for j in c])
+            theta, V = rayleigh_ritz(Ht, Mt, len(c))
+            for a, j in enumerate(c):
+                tx = [(V[b, a], idt, Y[c[b]]) for b in range(len(c))]
+                Xn[j] = normalize(tree, fit(tree, tx, fit_initial(tx), fit_sweeps))
+                lam_n[j] = theta[a]
+        X, lam = Xn, lam_n
+        hist.append(lam.copy())
+    return lam, X, hist

@@ -1348,6 +1348,138 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
   CUDA_CHECK(cudaStreamSynchronize(st));
 }
 
+// Single-linkage blocks of the Rayleigh quotients (sorted values closer than `gap` join); gap <= 0
+// gives one block per state.
+static std::vector<std::vector<int>> clusters_by_gap(const std::vector<double>& lam, double gap) {
+  const int n = (int)lam.size();
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lam[a] < lam[b]; });
+  std::vector<std::vector<int>> out;
+  for (int k = 0; k < n; ++k) {
+    if (k > 0 && gap > 0.0 && lam[order[k]] - lam[order[k - 1]] < gap) out.back().push_back(order[k]);
+    else out.push_back({order[k]});
+  }
+  for (auto& c : out) std::sort(c.begin(), c.end());
+  return out;
+}
+
+// Block inverse iteration (Alg. 3): every block uses the mean Rayleigh quotient of its states as
+// the shift; every state is solved by ALS; blocks of more than one state are re-orthogonalised
+// by their own Rayleigh-Ritz step and refitted.
+template <class T>
+static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter,
+                                   double gap, int als_sweeps, int mr_max, double mr_tol,
+                                   int fit_sweeps, int prec, double* eig_hist, bool& hit) {
+  const TreeInfo& tr = x->tree;
+  const int n = x->n_states;
+  cudaStream_t st = ctx->stream;
+  ttn_ttno* Id = identity_for(ctx, tr);
+  std::vector<int> id(n);
+  std::iota(id.begin(), id.end(), 0);
+  auto new_block = [&](int ns) {
+    ttn_tree tmp;
+    tmp.ctx = ctx;
+    tmp.info = tr;
+    ttn_block* b = nullptr;
+    ttn_status s = ttn_block_create(ctx, &tmp, ns, x->bond.data(), &b);
+    if (s != TTN_OK) TTN_FAIL(s, "%s", ctx->last_error.c_str());
+    return std::unique_ptr<ttn_block>(b);
+  };
+  auto diag = [&](ttn_ttno* op, const ttn_block* b) {
+    DevBuf dv((size_t)n * sizeof(double), st);
+    gram_pairs<T>(ctx, op, b, b, id, id, dv.as<double>());
+    std::vector<double> h(n);
+    CUDA_CHECK(cudaMemcpyAsync(h.data(), dv.p, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+    return h;
+  };
+  normalize_states<T>(ctx, x, prec);
+  std::vector<double> lam = diag(H, x);
+  if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist);
+  auto Y = new_block(n), Xn = new_block(n);
+  const double rr_eps = prec == TTN_FP64 ? 1e-12 : 1e-6;
+  for (int it = 1; it <= n_iter; ++it) {
+    const auto blocks = clusters_by_gap(lam, gap);
+    std::vector<double> shift(n);
+    for (const auto& c : blocks) {
+      double m = 0.0;
+      for (int j : c) m += lam[j];
+      for (int j : c) shift[j] = m / c.size();
+    }
+    {
+      PhaseScope ph(ctx, "als_inverse");
+      ttn_status cs = ttn_block_copy_states(Y.get(), x, n, id.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      hit |= als_impl<T>(ctx, H, shift, x, Y.get(), als_sweeps, mr_max, mr_tol);
+      normalize_states<T>(ctx, Y.get(), prec);
+    }
+    std::vector<double> lam_n = diag(H, Y.get());
+    {
+      ttn_status cs = ttn_block_copy_states(Xn.get(), Y.get(), n, id.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+    }
+    for (const auto& c : blocks) {
+      const int m = (int)c.size();
+      if (m == 1) continue;
+      PhaseScope ph(ctx, "block_rayleigh_ritz");
+      auto Yc = new_block(m), Xc = new_block(m);
+      ttn_status cs = ttn_block_copy_states(Yc.get(), Y.get(), m, c.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      DevBuf Ht((size_t)m * m * sizeof(double), st), Mt((size_t)m * m * sizeof(double), st),
+          th((size_t)m * sizeof(double), st), V((size_t)m * m * sizeof(double), st);
+      CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
+      CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
+      gram_device(ctx, H, Yc.get(), Yc.get(), Ht.as<double>(), m, prec);
+      gram_device(ctx, Id, Yc.get(), Yc.get(), Mt.as<double>(), m, prec);
+      rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), m, rr_eps, th.as<double>(),
+                           V.as<double>());
+      std::vector<double> hth(m), hV((size_t)m * m);
+      CUDA_CHECK(cudaMemcpyAsync(hth.data(), th.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaMemcpyAsync(hV.data(), V.p, hV.size() * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+      CUDA_CHECK(cudaStreamSynchronize(st));
+      FitGroup g{Id, Yc.get(), {}, {}, {}};
+      std::vector<int> init(m);
+      for (int a = 0; a < m; ++a) {
+        int arg = 0;
+        double best = -1.0;
+        for (int b = 0; b < m; ++b) {
+          const double v = hV[(size_t)b * m + a];
+          if (std::fabs(v) > best) {
+            best = std::fabs(v);
+            arg = b;
+          }
+          if (v != 0.0) {
+            g.out_j.push_back(a);
+            g.in_k.push_back(b);
+            g.coef.push_back(v);
+          }
+        }
+        init[a] = arg;
+      }
+      cs = ttn_block_copy_states(Xc.get(), Yc.get(), m, init.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+      std::vector<FitGroup> gs{g};
+      fit_impl<T>(ctx, gs, Xc.get(), fit_sweeps);
+      normalize_states<T>(ctx, Xc.get(), prec);
+      for (int a = 0; a < m; ++a) {
+        lam_n[c[a]] = hth[a];
+        for (int t = 0; t < tr.n; ++t)
+          CUDA_CHECK(cudaMemcpyAsync(Xn->node64(t) + (long long)c[a] * Xn->size[t],
+                                     Xc->node64(t) + (long long)a * Xc->size[t],
+                                     Xn->size[t] * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+      Xn->touch();
+    }
+    ttn_status cs = ttn_block_copy_states(x, Xn.get(), n, id.data());
+    if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+    lam = lam_n;
+    if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist + (size_t)it * n);
+  }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
 // ------------------------------------------------------------------------------------------------
 // Rayleigh-Ritz without device allocation.
 //
@@ -1489,6 +1621,30 @@ ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
     else
       lobpcg_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
                          minres_max, minres_tol, fit_sweeps, prec, eig_hist, hit);
+    return hit ? TTN_ENOTCONV : TTN_OK;
+  });
+}
+
+ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
+                                 double cluster_gap, int als_sweeps, int minres_max,
+                                 double minres_tol, int fit_sweeps, ttn_precision prec,
+                                 double* rq_hist) {
+  if (!ctx || !H || !x) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    TTN_REQUIRE(n_iter >= 0 && als_sweeps >= 0 && minres_max >= 0 && fit_sweeps >= 0,
+                "bad solver settings");
+    TTN_REQUIRE(x->n_states >= 1, "empty block");
+    TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    bool hit = false;
+    if (prec == TTN_FP64)
+      inverse_iteration_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, cluster_gap,
+                                     als_sweeps, minres_max, minres_tol, fit_sweeps, prec,
+                                     rq_hist, hit);
+    else
+      inverse_iteration_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, cluster_gap,
+                                    als_sweeps, minres_max, minres_tol, fit_sweeps, prec,
+                                    rq_hist, hit);
     return hit ? TTN_ENOTCONV : TTN_OK;
   });
 }

@@ -67,6 +67,7 @@ _SIGS = {
     "ttn_rayleigh_ritz": (_I, [_P, _I, _DP, _DP, _I, _D, _DP, _DP]),
     "ttn_lobpcg": (_I, [_P, _P, _P, _I, _D, _I, _I, _D, _I, _I, _DP]),
     "ttn_rayleigh_ritz_noalloc": (_I, [_P, _I, _P, _P, _I, _D, _P, _P]),
+    "ttn_inverse_iteration": (_I, [_P, _P, _P, _I, _D, _I, _I, _D, _I, _I, _DP]),
 }
 
 
@@ -436,6 +437,17 @@ def ttn_lobpcg(ctx, H, x, n_iter, shift_offset, als_sweeps=2, minres_max=10, min
     st = load().ttn_lobpcg(ctx.ptr, H.ptr, x.ptr, int(n_iter), float(shift_offset),
                            int(als_sweeps), int(minres_max), float(minres_tol), int(fit_sweeps),
                            _prec(prec), _dp(hist))
+    if st not in (0, 5):
+        ctx.check(st)
+    return hist
+
+
+def ttn_inverse_iteration(ctx, H, x, n_iter, cluster_gap=0.0, als_sweeps=1, minres_max=10000,
+                          minres_tol=1e-5, fit_sweeps=2, prec="fp64"):
+    hist = np.zeros((n_iter + 1, x.n_states))
+    st = load().ttn_inverse_iteration(ctx.ptr, H.ptr, x.ptr, int(n_iter), float(cluster_gap),
+                                      int(als_sweeps), int(minres_max), float(minres_tol),
+                                      int(fit_sweeps), _prec(prec), _dp(hist))
     if st not in (0, 5):
         ctx.check(st)
     return hist

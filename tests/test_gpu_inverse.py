@@ -1,0 +1,77 @@
+"""Block inverse iteration (Alg. 3, Eq. inverse iteration update) on the GPU against the FP64
+oracle: one shift per state (the all-physical-tree configuration) and the paper's clustering of
+Rayleigh quotients into blocks with a mean shift (Sec. III.B).
+
+MINRES runs with tolerance 0 so both sides take the same Krylov steps. The shifted local systems
+are nearly singular by design (the shift is a Rayleigh quotient), so node tensors are compared
+only through the Rayleigh quotients, which are quadratic in the state error: 1e-8 relative."""
+import numpy as np
+import pytest
+
+from oracle import network as N, solvers as S
+from paper_2512_15875_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2512_15875_gb300 import ttn
+    ttn.load()
+    return ttn
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.ttn_create(0)
+
+
+def _run(T, ctx, tree, ham, bonds, n, gap, n_iter, noise=1e-2, als_sweeps=1, mr=10):
+    th = T.ttn_tree_create(ctx, tree)
+    H, _ = T.ttn_build_ttno(ctx, th, ham.flat(tree))
+    blk = I.initial_block(tree, ham, bonds, n, seed=1, noise=noise)
+    bX = T.block_from_arrays(ctx, th, bonds, blk)
+    hist = T.ttn_inverse_iteration(ctx, H, bX, n_iter, cluster_gap=gap, als_sweeps=als_sweeps,
+                                   minres_max=mr, minres_tol=0.0, prec="fp64")
+    otn = N.build_ttno(tree, ham)
+    X0 = [[t[j] for t in blk] for j in range(n)]
+    clusters = (lambda l: [[j] for j in range(len(l))]) if gap <= 0 else \
+        (lambda l: S.clusters_by_gap(l, gap))
+    _, _, ref = S.inverse_iteration(tree, otn, X0, n_iter, clusters, als_sweeps=als_sweeps,
+                                    minres_max=mr, minres_tol=0.0)
+    return hist, np.array(ref)
+
+
+@pytest.mark.parametrize("gap", [0.0, 300.0])
+def test_inverse_iteration_matches_oracle_on_the_four_mode_model(T, ctx, gap):
+    w = I.make_workload("c1", D=8)
+    hist, ref = _run(T, ctx, w.tree, w.ham, w.bonds, 5, gap, 2)
+    assert np.abs(hist - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_inverse_iteration_on_an_all_physical_binary_tree(T, ctx):
+    tree = I.all_physical_binary_tree(5, 4)
+    rng = np.random.default_rng(3)
+    ham = I.Hamiltonian(dims=[4] * 5, omega=rng.uniform(1000, 2000, 5))
+    for i in range(5):
+        ham.add(ham.omega[i], {i: "h"})
+    for i in range(5):
+        for j in range(i + 1, 5):
+            ham.add_monomial(rng.normal(0, 30), (i, j))
+    for _ in range(6):
+        ham.add_monomial(rng.normal(0, 5), tuple(sorted(rng.integers(0, 5, 3))))
+    bonds = I.uniform_bonds(tree, 8)
+    hist, ref = _run(T, ctx, tree, ham, bonds, 6, 0.0, 2)
+    assert np.abs(hist - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_inverse_iteration_converges_to_eigenvalues_at_full_bond(T, ctx):
+    w = I.make_workload("c1", D=36)
+    ev = np.linalg.eigvalsh(N.dense_hamiltonian(w.ham))
+    th = T.ttn_tree_create(ctx, w.tree)
+    H, _ = T.ttn_build_ttno(ctx, th, w.ham.flat(w.tree))
+    bX = T.block_from_arrays(ctx, th, w.bonds, w.block(noise=1e-2))
+    hist = T.ttn_inverse_iteration(ctx, H, bX, 4, cluster_gap=0.0, als_sweeps=2, minres_max=300,
+                                   minres_tol=1e-12, prec="fp64")
+    for lam in hist[-1]:
+        assert np.abs(ev - lam).min() <= 1e-8 * abs(lam)
