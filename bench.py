@@ -50,11 +50,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=12)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "fp64"])
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--mode", default="lobpcg", choices=["lobpcg", "gram"],
+    ap.add_argument("--mode", default="lobpcg", choices=["lobpcg", "gram", "accuracy"],
                     help="lobpcg: a step is one block-LOBPCG iteration (the headline); gram: a "
-                         "step is one 3n-state Gram (H and S), for kernel profiling")
+                         "step is one 3n-state Gram (H and S), for kernel profiling; accuracy: "
+                         "K iterations in --precision and in float64 from the same block, "
+                         "per-state difference of the Ritz values")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,6 +174,19 @@ def roofline_of(prof, precision):
     return rl
 
 
+def aggregate_replicas(t, n_conv, dist, device="cpu"):
+    """Whole-job numbers of independent replicas: the slowest rank's time and the states
+    converged on all ranks (no collective touches the data path; this is bookkeeping)."""
+    if dist is None:
+        return t, n_conv
+    import torch
+    tmax = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    nsum = torch.tensor([float(n_conv)], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(nsum, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), int(nsum.item())
+
+
 def converged(hist):
     return int(np.sum(np.abs(hist[-1] - hist[-2]) <= CONV_TOL))
 
@@ -198,6 +213,18 @@ def gpu_arm(args, rank, world, local, dist):
 
     if args.mode == "gram":
         return gram_arm(args, T, ctx, th, H, w, stream, local, dist)
+    if args.mode == "accuracy":
+        res = {}
+        for prec in (args.precision, "fp64"):
+            x = fresh()
+            t0 = time.perf_counter()
+            res[prec] = (T.ttn_lobpcg(ctx, H, x, args.steps, SHIFT_OFFSET, **dict(kw, prec=prec)),
+                         time.perf_counter() - t0)
+        hm, tm = res[args.precision]
+        hd, td = res["fp64"]
+        err = np.abs(hm[-1] - hd[-1])
+        return dict(accuracy=True, err=err, t_mixed=tm, t_fp64=td, n=n,
+                    conv_mixed=converged(hm), conv_fp64=converged(hd))
     # warm-up: W iterations on a copy
     xw = fresh()
     T.ttn_lobpcg(ctx, H, xw, args.warmup, SHIFT_OFFSET, **kw)
@@ -379,18 +406,23 @@ def main():
             reference_arm(args)
         return
     out = gpu_arm(args, rank, world, local, dist)
-    t, n_conv = out["t"], out["n_conv"]
-    if dist:
-        import torch
-        tt = torch.tensor([t, float(n_conv)], device=f"cuda:{local}", dtype=torch.float64)
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        nsum = tt[1:].clone()
-        dist.all_reduce(nsum, op=dist.ReduceOp.SUM)
-        t, n_conv = float(tmax.item()), int(nsum.item())
+    t, n_conv = aggregate_replicas(out.get("t", 0.0), out.get("n_conv", 0), dist,
+                                   f"cuda:{local}" if dist else "cpu")
     if rank != 0:
         return
     w = workload(args.workload)
+    if out.get("accuracy"):
+        e = out["err"]
+        print(json.dumps({"mode": "accuracy", "workload": f"{args.workload}: {w.description}",
+                          "iterations": args.steps, "precision": args.precision,
+                          "max_abs_diff_cm1": float(e.max()), "mean_abs_diff_cm1": float(e.mean()),
+                          "states_within_0.1_cm1": int(np.sum(e <= 0.1)), "of": out["n"],
+                          "per_state_abs_diff_cm1": [round(float(v), 6) for v in e],
+                          "wall_s": {args.precision: out["t_mixed"], "fp64": out["t_fp64"]},
+                          "speedup_vs_fp64": out["t_fp64"] / out["t_mixed"],
+                          "converged_states": {args.precision: out["conv_mixed"],
+                                               "fp64": out["conv_fp64"]}}))
+        return
     if out.get("gram_mode"):
         rl = roofline_of(out["prof"], args.precision)
         print(json.dumps({"mode": "gram", "metric": "Gram contraction TFLOP/s", "value":
@@ -410,7 +442,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "dtype": {"fp32": "f32", "tf32x3": "f32 (tf32x3 tensor-core levels)",
+                  "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w.description}, n={w.n_states}",
                    "subspace": 3 * w.n_states, "ttno_max_bond": max(out["wbond"]),
                    "steps_are": "block-LOBPCG iterations from the initial block",

@@ -46,8 +46,11 @@ typedef enum {
 
 typedef enum {
   TTN_FP64 = 0,   /* every contraction in float64 */
-  TTN_FP32 = 1    /* node contractions in float32 with float32 accumulation; Gram closure,
+  TTN_FP32 = 1,   /* node contractions in float32 with float32 accumulation; Gram closure,
                      Lanczos/MINRES scalars and Rayleigh-Ritz in float64 */
+  TTN_TF32X3 = 2  /* as TTN_FP32, but the level stages of the node contractions run on the
+                     tensor cores as TF32 products with the 3xTF32 split (x = hi + lo, three
+                     products per term) and float32 accumulation */
 } ttn_precision;
 
 #define TTN_MAX_LEGS 8   /* stride of per-entry w-tuples in the TTNO entry arrays */

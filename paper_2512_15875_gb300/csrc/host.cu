@@ -863,10 +863,11 @@ ttn_status ttn_env_update(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra
                           ttn_precision prec) {
   if (!ctx || !envs) return TTN_EINVAL;
   return guarded(ctx, [&] {
+    PrecisionScope prec_scope(ctx, prec);
     check_pair_blocks(Hc, bra, ket);
     TTN_REQUIRE(envs->tree.same_shape(bra->tree), "envs created for another tree");
     TTN_REQUIRE(direction >= 0 && direction <= 2, "direction must be 0, 1 or 2");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision %d", (int)prec);
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision %d", (int)prec);
     TTN_REQUIRE(n_pairs >= 0 && (n_pairs == 0 || (pair_bra && pair_ket)), "pairs");
     for (int i = 0; i < n_pairs; ++i)
       TTN_REQUIRE(pair_bra[i] >= 0 && pair_bra[i] < bra->n_states && pair_ket[i] >= 0 &&
@@ -1043,6 +1044,7 @@ ttn_status ttn_heff_apply(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_envs* envs
                           ttn_precision prec) {
   if (!ctx || !Hc || !envs || !x || !y) return TTN_EINVAL;
   return guarded(ctx, [&] {
+    PrecisionScope prec_scope(ctx, prec);
     ttn_ttno* H = const_cast<ttn_ttno*>(Hc);
     check_pair_blocks(H, x, y);
     TTN_REQUIRE(node >= 0 && node < x->tree.n, "bad node");
@@ -1089,10 +1091,11 @@ ttn_status ttn_gram(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra, cons
                     double* S, double* Hm, int ld, int out_on_device, ttn_precision prec) {
   if (!ctx || !bra || !ket) return TTN_EINVAL;
   return guarded(ctx, [&] {
+    PrecisionScope prec_scope(ctx, prec);
     check_pair_blocks(Hc, bra, ket);
     TTN_REQUIRE(bra->bond == ket->bond || bra != ket, "internal");
     TTN_REQUIRE(ld >= ket->n_states, "ld < number of ket states");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision %d", (int)prec);
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision %d", (int)prec);
     const size_t mat = (size_t)bra->n_states * ld;
     auto one = [&](ttn_ttno* H, double* out) {
       if (!out) return;

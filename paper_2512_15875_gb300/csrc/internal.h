@@ -99,7 +99,20 @@ struct ttn_ctx {
   std::vector<LaunchRecord> prof;
   std::vector<cudaEvent_t> event_pool;
   double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
+  bool tf32x3 = false;           // float32 calls route level stages to tensor cores
 };
+
+// Sets ctx->tf32x3 for the duration of one entry-point call.
+struct PrecisionScope {
+  ttn_ctx* ctx;
+  bool saved;
+  PrecisionScope(ttn_ctx* c, int prec) : ctx(c), saved(c->tf32x3) {
+    ctx->tf32x3 = prec == TTN_TF32X3;
+  }
+  ~PrecisionScope() { ctx->tf32x3 = saved; }
+};
+// float64 for TTN_FP64, float32 otherwise
+inline bool is_fp64(int prec) { return prec == TTN_FP64; }
 
 // RAII helper: records the launch's events (if profiling) and counts it.
 struct LaunchScope {
@@ -270,6 +283,9 @@ void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long
 // Specialised level-stage GEMM (a_sm = 1, N, K <= 64; items sum over their segments).
 bool level_shape_ok(const GemmDesc& g);
 template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
+// Tensor-core (TF32 MMA, 3xTF32 split) level stage for float data, N <= 32, K <= 64.
+bool level_tc_ok(const GemmDesc& g);
+void launch_level_tc(ttn_ctx* ctx, const GemmDesc& g);
 // Specialised closure GEMM (one segment per item, a_sk = b_sk = 1, M, N <= 32).
 bool closure_shape_ok(const GemmDesc& g);
 template <class T> void launch_closure(ttn_ctx* ctx, const GemmDesc& g);

@@ -1,5 +1,6 @@
 // Generic device kernels of the contraction engine: a strided batched GEMM with per-item
 // segment sums (the workhorse of every node contraction), tensor permutes, per-pair dots.
+#include <cstdint>
 #include <cstdio>
 #include <set>
 
@@ -673,6 +674,10 @@ template void launch_combine_env<float>(ttn_ctx*, const float*, long long, long 
 template <class T>
 void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  if (sizeof(T) == 4 && ctx->tf32x3 && level_tc_ok(g)) {
+    launch_level_tc(ctx, g);
+    return;
+  }
   TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
   check_bounds(g, sizeof(T));
   const int rtiles = (g.M + kThreads - 1) / kThreads;
@@ -806,6 +811,136 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
 
 template void launch_closure<double>(ttn_ctx*, const GemmDesc&);
 template void launch_closure<float>(ttn_ctx*, const GemmDesc&);
+
+// ---- level stage on tensor cores: TF32 MMA with the 3xTF32 split ------------------------------
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi); a*b ~ hi_a*hi_b + hi_a*lo_b + lo_a*hi_b with
+// float32 accumulation, which keeps ~2^-21 relative accuracy per product (plain TF32 would give
+// ~2^-11). Fragments follow the m16n8k8 .row.col layout: groupID g = lane/4, t = lane%4;
+// A: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4); B: b0 (k=t, n=g), b1 (k=t+4, n=g);
+// C: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// out[r][a] = sum_b in[b][r] E[a][b]: rows r -> MMA rows (16 per warp, 128 per CTA), a -> 8-wide
+// n tiles (NT of them), b -> 8-deep k steps (KS of them). The environment slice is staged in
+// shared memory as Es[n][k] (row length KS*8 + 4: conflict-free fragment loads); the output
+// tile goes through a padded shared tile for coalesced stores.
+template <int NT, int KS>
+__global__ void __launch_bounds__(kThreads) level_tc_kernel(GemmDesc g, int rtiles) {
+  constexpr int NP = NT * 8, KP = KS * 8, LDE = KP + 4, LDO = NP + 1, ROWS = 128;
+  __shared__ __align__(16) float Es[NP * LDE];
+  __shared__ float Os[ROWS * LDO];
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3;
+  const int r0 = rt * ROWS;
+  const int rw = r0 + warp * 16;                  // first row of this warp
+  float acc[NT][4];
+#pragma unroll
+  for (int j = 0; j < NT; ++j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+  for (int seg = g.st.seg_ptr[sub]; seg < g.st.seg_ptr[sub + 1]; ++seg) {
+    const float* Ab = Abase + g.st.seg_a[seg];
+    const float* Bb = Bbase + g.st.seg_b[seg];
+    __syncthreads();
+    for (int i = threadIdx.x; i < NP * KP; i += kThreads) {
+      const int n = i / KP, k = i % KP;
+      Es[n * LDE + k] = (n < g.N && k < g.K) ? Bb[(long long)n * g.b_sn + (long long)k * g.b_sk]
+                                             : 0.f;
+    }
+    __syncthreads();
+    const bool r_lo = rw + gq < g.M, r_hi = rw + gq + 8 < g.M;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const int k0 = ks * 8 + tq, k1 = k0 + 4;
+      const float x0 = (r_lo && k0 < g.K) ? Ab[(long long)k0 * g.a_sk + rw + gq] : 0.f;
+      const float x1 = (r_hi && k0 < g.K) ? Ab[(long long)k0 * g.a_sk + rw + gq + 8] : 0.f;
+      const float x2 = (r_lo && k1 < g.K) ? Ab[(long long)k1 * g.a_sk + rw + gq] : 0.f;
+      const float x3 = (r_hi && k1 < g.K) ? Ab[(long long)k1 * g.a_sk + rw + gq + 8] : 0.f;
+      uint32_t ah[4], al[4];
+      split_tf32(x0, ah[0], al[0]);
+      split_tf32(x1, ah[1], al[1]);
+      split_tf32(x2, ah[2], al[2]);
+      split_tf32(x3, ah[3], al[3]);
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const float* e = Es + (j * 8 + gq) * LDE + ks * 8 + tq;
+        uint32_t bh[2], bl[2];
+        split_tf32(e[0], bh[0], bl[0]);
+        split_tf32(e[4], bh[1], bl[1]);
+        mma_tf32(acc[j], al, bh);
+        mma_tf32(acc[j], ah, bl);
+        mma_tf32(acc[j], ah, bh);
+      }
+    }
+  }
+  // stage and store
+  const int lr = warp * 16 + gq;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    Os[lr * LDO + j * 8 + 2 * tq] = acc[j][0];
+    Os[lr * LDO + j * 8 + 2 * tq + 1] = acc[j][1];
+    Os[(lr + 8) * LDO + j * 8 + 2 * tq] = acc[j][2];
+    Os[(lr + 8) * LDO + j * 8 + 2 * tq + 1] = acc[j][3];
+  }
+  __syncthreads();
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  float* dst = static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] + (long long)r0 * g.c_sm;
+  const int nrow = min(ROWS, g.M - r0);
+  for (int i = threadIdx.x; i < nrow * g.N; i += kThreads)
+    dst[i] = Os[(i / g.N) * LDO + (i % g.N)];
+}
+
+bool level_tc_ok(const GemmDesc& g) { return level_shape_ok(g) && g.N <= 32 && g.K <= 64; }
+
+void launch_level_tc(ttn_ctx* ctx, const GemmDesc& g) {
+  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  TTN_REQUIRE(level_tc_ok(g), "tensor-core level kernel: unsupported shape");
+  check_bounds(g, sizeof(float));
+  const int rtiles = (g.M + 127) / 128;
+  const long long grid = (long long)rtiles * g.st.n_sub * g.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+  long long nseg = 0;
+  for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
+  const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
+  LaunchScope ls(ctx, "level_tf32x3", flops, algorithmic_bytes(g, sizeof(float)));
+  const int nt = (g.N + 7) / 8, ks = (g.K + 7) / 8;
+  cudaStream_t s = ctx->stream;
+#define TTN_LTC(NTv, KSv) \
+  if (nt == NTv && ks == KSv) { level_tc_kernel<NTv, KSv><<<grid, kThreads, 0, s>>>(g, rtiles); }
+#define TTN_LTC_K(NTv) TTN_LTC(NTv, 1) else TTN_LTC(NTv, 2) else TTN_LTC(NTv, 3) else \
+  TTN_LTC(NTv, 4) else TTN_LTC(NTv, 5) else TTN_LTC(NTv, 6) else TTN_LTC(NTv, 7) else TTN_LTC(NTv, 8)
+  TTN_LTC_K(1) else TTN_LTC_K(2) else TTN_LTC_K(3) else TTN_LTC_K(4)
+#undef TTN_LTC_K
+#undef TTN_LTC
+  CUDA_LAUNCH_CHECK();
+}
 
 template void launch_level<double>(ttn_ctx*, const GemmDesc&);
 template void launch_level<float>(ttn_ctx*, const GemmDesc&);

@@ -1530,10 +1530,11 @@ ttn_status ttn_recompress(ttn_ctx* ctx, int n_in, const double* coeff, const ttn
                           int n_out, int n_sweeps, ttn_precision prec) {
   if (!ctx || !out) return TTN_EINVAL;
   return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
     TTN_REQUIRE(n_in >= 0 && (n_in == 0 || (coeff && ops && in && in_state)), "inputs");
     TTN_REQUIRE(n_out == out->n_states, "n_out must equal the states of `out`");
     TTN_REQUIRE(n_sweeps >= 0, "n_sweeps < 0");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
     std::vector<FitGroup> groups;
     for (int k = 0; k < n_in; ++k) {
       check_block_like(in[k], out);
@@ -1568,11 +1569,12 @@ ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
                          double minres_tol, ttn_precision prec) {
   if (!ctx || !H || !shift || !rhs || !y) return TTN_EINVAL;
   return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
     check_block_like(rhs, y);
     TTN_REQUIRE(rhs->n_states == y->n_states, "rhs and y differ in state count");
     TTN_REQUIRE(H->tree.same_shape(y->tree), "operator on another tree");
     TTN_REQUIRE(n_sweeps >= 0 && minres_max >= 0 && minres_tol >= 0.0, "bad solver settings");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
     std::vector<double> s(shift, shift + y->n_states);
     bool hit = prec == TTN_FP64
                    ? als_impl<double>(ctx, const_cast<ttn_ttno*>(H), s, rhs, y, n_sweeps,
@@ -1609,11 +1611,12 @@ ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
                       int fit_sweeps, ttn_precision prec, double* eig_hist) {
   if (!ctx || !H || !x) return TTN_EINVAL;
   return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
     TTN_REQUIRE(n_iter >= 0 && als_sweeps >= 0 && minres_max >= 0 && fit_sweeps >= 0,
                 "bad solver settings");
     TTN_REQUIRE(x->n_states >= 1, "empty block");
     TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
     bool hit = false;
     if (prec == TTN_FP64)
       lobpcg_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
@@ -1631,11 +1634,12 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
                                  double* rq_hist) {
   if (!ctx || !H || !x) return TTN_EINVAL;
   return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
     TTN_REQUIRE(n_iter >= 0 && als_sweeps >= 0 && minres_max >= 0 && fit_sweeps >= 0,
                 "bad solver settings");
     TTN_REQUIRE(x->n_states >= 1, "empty block");
     TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32, "unknown precision");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
     bool hit = false;
     if (prec == TTN_FP64)
       inverse_iteration_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, cluster_gap,

@@ -27,7 +27,7 @@ def ctx(T):
 
 
 @pytest.mark.parametrize("name", ["c3", "c4", "c5"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_full_size_gram_sampled(T, ctx, name, prec):
     w = I.make_workload(name)
     th = T.ttn_tree_create(ctx, w.tree)

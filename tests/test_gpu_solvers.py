@@ -166,13 +166,14 @@ def test_lobpcg_matches_oracle_fp64(T, ctx):
         assert _rel(hist[it], ref_hist[it]) <= 1e-10, it
 
 
-def test_lobpcg_fp32_within_a_tenth_of_a_wavenumber(T, ctx):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_lobpcg_reduced_precision_within_a_tenth_of_a_wavenumber(T, ctx, prec):
     w, th, H = _c1(T, ctx)
     otn = N.build_ttno(w.tree, w.ham)
     blk = w.block()
     X0 = _states(blk, w.n_states)
     bX = T.block_from_arrays(ctx, th, w.bonds, blk)
-    hist = T.ttn_lobpcg(ctx, H, bX, 3, -100.0, minres_tol=0.0, prec="fp32")
+    hist = T.ttn_lobpcg(ctx, H, bX, 3, -100.0, minres_tol=0.0, prec=prec)
     _, _, ref_hist = S.lobpcg(w.tree, otn, X0, 3, shift=lambda l: np.min(l) - 100.0,
                               minres_tol=0.0)
     err = np.abs(hist[-1] - ref_hist[-1])
