@@ -100,6 +100,7 @@ struct ttn_ctx {
   std::vector<cudaEvent_t> event_pool;
   double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
   bool tf32x3 = false;           // float32 calls route level stages to tensor cores
+  bool capturing = false;        // a CUDA graph is being captured on the stream (no events)
 };
 
 // Sets ctx->tf32x3 for the duration of one entry-point call.

@@ -276,7 +276,7 @@ static cudaEvent_t pool_event(ttn_ctx* ctx) {
 LaunchScope::LaunchScope(ttn_ctx* c, const char* name, double flops, double bytes) : ctx(c) {
   ctx->launches++;
   ctx->flops_total += flops;
-  if (!ctx->profiling) return;
+  if (!ctx->profiling || ctx->capturing) return;
   int id = -1;
   for (size_t i = 0; i < ctx->prof_names.size(); ++i)
     if (ctx->prof_names[i] == name) id = (int)i;
@@ -295,7 +295,7 @@ LaunchScope::~LaunchScope() {
 }
 
 PhaseScope::PhaseScope(ttn_ctx* c, const char* name) : ctx(c) {
-  if (!ctx->profiling) return;
+  if (!ctx->profiling || ctx->capturing) return;
   const std::string full = std::string("phase:") + name;
   int id = -1;
   for (size_t i = 0; i < ctx->prof_names.size(); ++i)

@@ -944,7 +944,9 @@ static bool minres_batched(ttn_ctx* ctx, ttn_ttno* H, EnvCache<T>& env, int t,
                                                       w1, w2, sz, n);
     CUDA_LAUNCH_CHECK();
   }
-  for (int it = 0; it < maxiter; ++it) {
+  // One MINRES step touches only device state at fixed addresses, so it is captured once as a
+  // CUDA graph and replayed (the planning work of the contraction runs once, at capture).
+  auto one_step = [&]() {
     matvec(v, p);
     launch_dot<T>(ctx, v, p, sz, n, d1.as<double>());
     {
@@ -965,6 +967,48 @@ static bool minres_batched(ttn_ctx* ctx, ttn_ttno* H, EnvCache<T>& env, int t,
       mr_step_vectors<T><<<grid_of(total), kT, 0, st>>>(sc.as<double>(), x, v, vp, w1, w2, p,
                                                         sz, n);
       CUDA_LAUNCH_CHECK();
+    }
+  };
+  cudaGraphExec_t exec = nullptr;
+  long long step_launches = 0;
+  double step_flops = 0.0;
+  if (maxiter > 1) {
+    cudaGraph_t graph = nullptr;
+    const long long l0 = ctx->launches;
+    const double f0 = ctx->flops_total;
+    CUDA_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    ctx->capturing = true;
+    try {
+      one_step();
+    } catch (...) {
+      ctx->capturing = false;
+      cudaStreamEndCapture(st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    ctx->capturing = false;
+    CUDA_CHECK(cudaStreamEndCapture(st, &graph));
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_CHECK(ie);
+    step_launches = ctx->launches - l0;
+    step_flops = ctx->flops_total - f0;
+    ctx->launches = l0;
+    ctx->flops_total = f0;
+  }
+  struct ExecGuard {
+    cudaGraphExec_t e;
+    ~ExecGuard() {
+      if (e) cudaGraphExecDestroy(e);
+    }
+  } exec_guard{exec};
+  for (int it = 0; it < maxiter; ++it) {
+    if (exec) {
+      CUDA_CHECK(cudaGraphLaunch(exec, st));
+      ctx->launches += step_launches;
+      ctx->flops_total += step_flops;
+    } else {
+      one_step();
     }
     if (maxiter > 32 && (it + 1) % 16 == 0) {
       std::vector<double> h((size_t)n * MR_NFIELDS);
