@@ -550,7 +550,7 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
 // the environment slice is staged transposed (Es[b][a], zero-padded to NA) in shared memory and
 // read with broadcast vector loads; each item has exactly one segment.
 template <class T, int NA>
-__global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles, int tiles_per_cta) {
+__global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles) {
   constexpr int KMAX = 64;
   // the output tile (kThreads rows x NA, rows contiguous in global memory) is staged through a
   // padded shared buffer so the global stores are coalesced; only where it fits statically
@@ -558,81 +558,69 @@ __global__ void __launch_bounds__(kThreads) level_kernel(GemmDesc g, int rtiles,
   constexpr int kOutLd = NA + 1;
   __shared__ __align__(16) T Es[KMAX * NA];
   __shared__ T Os[kStage ? kThreads * kOutLd : 1];
-  // blockIdx -> (pair, sub, group of tiles_per_cta row tiles)
-  const int groups = (rtiles + tiles_per_cta - 1) / tiles_per_cta;
   const long long bid = blockIdx.x;
-  const int rg = (int)(bid % groups);
-  const long long rest = bid / groups;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
   const int sub = (int)(rest % g.st.n_sub);
   const int pair = (int)(rest / g.st.n_sub);
   const T* Abase = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket);
   const T* Bbase = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket);
+  const int r0 = rt * kThreads;
+  const int r = r0 + threadIdx.x;
+  const bool live = r < g.M;
+  T acc[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) acc[a] = T(0);
+  for (int seg = g.st.seg_ptr[sub]; seg < g.st.seg_ptr[sub + 1]; ++seg) {
+  const T* Ab = Abase + g.st.seg_a[seg];
+  const T* Bb = Bbase + g.st.seg_b[seg];
+  __syncthreads();
+  for (int i = threadIdx.x; i < g.K * NA; i += kThreads) {
+    const int b = i / NA, a = i % NA;
+    Es[i] = a < g.N ? Bb[(long long)a * g.b_sn + (long long)b * g.b_sk] : T(0);
+  }
+  __syncthreads();
+  if (live) {
+    const T* src = Ab + r;
+    int b = 0;
+    for (; b + 8 <= g.K; b += 8) {
+      T t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = src[(long long)(b + u) * g.a_sk];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T* e = Es + (b + u) * NA;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t[u], acc[a]);
+      }
+    }
+    for (; b < g.K; ++b) {
+      const T t = src[(long long)b * g.a_sk];
+      const T* e = Es + b * NA;
+#pragma unroll
+      for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t, acc[a]);
+    }
+  }
+  }
   long long cidx = 0;
   if (g.c_mode == MODE_PAIR) cidx = pair;
   else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
   else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
   T* base = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
-  const int s0 = g.st.seg_ptr[sub], s1 = g.st.seg_ptr[sub + 1];
-  const bool single = s1 - s0 == 1;
-  const int rt_end = min(rtiles, (rg + 1) * tiles_per_cta);
-  for (int rt = rg * tiles_per_cta; rt < rt_end; ++rt) {
-    const int r0 = rt * kThreads;
-    const int r = r0 + threadIdx.x;
-    const bool live = r < g.M;
-    T acc[NA];
+  if constexpr (kStage) {
 #pragma unroll
-    for (int a = 0; a < NA; ++a) acc[a] = T(0);
-    for (int seg = s0; seg < s1; ++seg) {
-      const T* Ab = Abase + g.st.seg_a[seg];
-      if (!single || rt == rg * tiles_per_cta) {
-        // stage Es[b][a] = E[a][b]; global reads contiguous in b
-        const T* Bb = Bbase + g.st.seg_b[seg];
-        __syncthreads();
-        for (int i = threadIdx.x; i < g.K * NA; i += kThreads) {
-          const int a = i / g.K, b = i % g.K;
-          Es[b * NA + a] = a < g.N ? Bb[(long long)a * g.b_sn + (long long)b * g.b_sk] : T(0);
-        }
-        __syncthreads();
-      }
-      if (live) {
-        const T* src = Ab + r;
-        int b = 0;
-        for (; b + 8 <= g.K; b += 8) {
-          T t[8];
+    for (int a = 0; a < NA; ++a) Os[threadIdx.x * kOutLd + a] = acc[a];
+    __syncthreads();
+    const int nrow = min(kThreads, g.M - r0);
+    T* dst = base + (long long)r0 * g.c_sm;     // c_sm == N: the tile is contiguous
+    for (int i = threadIdx.x; i < nrow * g.N; i += kThreads)
+      dst[i] = Os[(i / g.N) * kOutLd + (i % g.N)];
+  } else {
+    if (!live) return;
+    T* dst = base + (long long)r * g.c_sm;
 #pragma unroll
-          for (int u = 0; u < 8; ++u) t[u] = src[(long long)(b + u) * g.a_sk];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const T* e = Es + (b + u) * NA;
-#pragma unroll
-            for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t[u], acc[a]);
-          }
-        }
-        for (; b < g.K; ++b) {
-          const T t = src[(long long)b * g.a_sk];
-          const T* e = Es + b * NA;
-#pragma unroll
-          for (int a = 0; a < NA; ++a) acc[a] = fma(e[a], t, acc[a]);
-        }
-      }
-    }
-    if constexpr (kStage) {
-      __syncthreads();
-#pragma unroll
-      for (int a = 0; a < NA; ++a) Os[threadIdx.x * kOutLd + a] = acc[a];
-      __syncthreads();
-      const int nrow = min(kThreads, g.M - r0);
-      T* dst = base + (long long)r0 * g.c_sm;     // c_sm == N: the tile is contiguous
-      for (int i = threadIdx.x; i < nrow * g.N; i += kThreads)
-        dst[i] = Os[(i / g.N) * kOutLd + (i % g.N)];
-    } else {
-      if (live) {
-        T* dst = base + (long long)r * g.c_sm;
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-          if (a < g.N) dst[a] = acc[a];
-      }
-    }
+    for (int a = 0; a < NA; ++a)
+      if (a < g.N) dst[a] = acc[a];
   }
 }
 
@@ -693,13 +681,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
   check_bounds(g, sizeof(T));
   const int rtiles = (g.M + kThreads - 1) / kThreads;
-  // items with one segment keep the staged environment slice for all their row tiles (up to
-  // 8 per CTA); items that sum several segments take one row tile per CTA
-  bool single = true;
-  for (int q = 0; q < g.st.n_sub && single; ++q)
-    single = g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q] == 1;
-  const int tpc = single ? std::min(rtiles, 8) : 1;
-  const long long grid = (long long)((rtiles + tpc - 1) / tpc) * g.st.n_sub * g.n_pairs;
+  const long long grid = (long long)rtiles * g.st.n_sub * g.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
   long long nseg = 0;
   for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
@@ -714,12 +696,12 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   LaunchScope ls(ctx, sizeof(T) == 8 ? n64[ci] : n32[ci], flops, bytes);
   cudaStream_t s = ctx->stream;
   switch (na) {
-    case 8: level_kernel<T, 8><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
-    case 16: level_kernel<T, 16><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
-    case 24: level_kernel<T, 24><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
-    case 32: level_kernel<T, 32><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
-    case 48: level_kernel<T, 48><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
-    default: level_kernel<T, 64><<<grid, kThreads, 0, s>>>(g, rtiles, tpc); break;
+    case 8: level_kernel<T, 8><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 16: level_kernel<T, 16><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 24: level_kernel<T, 24><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 32: level_kernel<T, 32><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    case 48: level_kernel<T, 48><<<grid, kThreads, 0, s>>>(g, rtiles); break;
+    default: level_kernel<T, 64><<<grid, kThreads, 0, s>>>(g, rtiles); break;
   }
   CUDA_LAUNCH_CHECK();
 }
@@ -746,7 +728,7 @@ __device__ __forceinline__ void load4(const double* p, double* v) {
 // tiles; shared tiles are k-major with a padded row (36) so 4-wide loads stay aligned; the four
 // partial sums are reduced through shared memory at the end.
 template <class T>
-__global__ void __launch_bounds__(kThreads, 3) closure_kernel(GemmDesc g) {
+__global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
   constexpr int KC = sizeof(T) == 8 ? 16 : 32, LD = 36;
   static_assert(2 * 4 * KC * LD >= 4096, "reduction buffer");
   __shared__ __align__(16) T sh[2 * 4 * KC * LD];
