@@ -256,7 +256,8 @@ def gpu_arm(args, rank, world, local, dist):
 
     # end-to-end through the public API with host buffers
     if not args.no_e2e:
-        host = [np.ascontiguousarray(a) for a in blk]
+        # inputs staged in pinned host memory, as a serving caller would hold them
+        host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in blk]
         h2d = sum(a.nbytes for a in host)
         xe = T.ttn_block_create(ctx, th, n, w.bonds)
         T.ttn_synchronize(ctx)

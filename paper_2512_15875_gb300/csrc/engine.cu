@@ -16,6 +16,7 @@
 // kept block-sparse: only distinct (w-prefix) and (prefix, w_open) combinations are contracted.
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <set>
 
 #include "internal.h"
@@ -210,6 +211,25 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
     }
     hs.push_back(std::move(s));
   }
+  // A groups of the level stages: single-segment items reading the same A slice, in chunks the
+  // bulk-copy level kernel stages at once
+  for (int l = 1; l <= mC; ++l) {
+    HostStage& s = hs[l - 1];
+    const int c = p.C[l - 1];
+    const int cap = level_group_cap((int)(sizes[l - 1] / Db[c]), Da[c], Db[c]);
+    bool single = cap > 0;
+    for (size_t j = 0; single && j + 1 < s.seg_ptr.size(); ++j)
+      single = s.seg_ptr[j + 1] - s.seg_ptr[j] == 1;
+    if (!single) continue;
+    std::map<long long, std::vector<int>> by_a;
+    for (int j = 0; j + 1 < (int)s.seg_ptr.size(); ++j) by_a[s.seg_a[s.seg_ptr[j]]].push_back(j);
+    for (auto& kv : by_a)
+      for (size_t i = 0; i < kv.second.size(); i += cap) {
+        const size_t e = std::min(kv.second.size(), i + (size_t)cap);
+        s.grp_sub.insert(s.grp_sub.end(), kv.second.begin() + i, kv.second.begin() + e);
+        s.grp_ptr.push_back((int)s.grp_sub.size());
+      }
+  }
   if (out_kind == OUT_ENV) {
     HostStage s;
     const int o = p.open;
@@ -226,7 +246,7 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
   size_t bytes = 0;
   for (auto& s : hs) {
     bytes += (s.sub_c.size() + s.seg_a.size() + s.seg_b.size()) * sizeof(long long);
-    bytes += s.seg_ptr.size() * sizeof(int) + 64;   // + alignment of 4 arrays
+    bytes += (s.seg_ptr.size() + s.grp_ptr.size() + s.grp_sub.size()) * sizeof(int) + 7 * 16;
   }
   std::vector<char> host(bytes + 64, 0);
   DevTables t;
@@ -247,6 +267,9 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
     ds.seg_ptr = (const int*)put(s.seg_ptr.data(), s.seg_ptr.size() * sizeof(int));
     ds.seg_a = (const long long*)put(s.seg_a.data(), s.seg_a.size() * sizeof(long long));
     ds.seg_b = (const long long*)put(s.seg_b.data(), s.seg_b.size() * sizeof(long long));
+    ds.n_grp = (int)s.grp_ptr.size() - 1;
+    ds.grp_ptr = (const int*)put(s.grp_ptr.data(), s.grp_ptr.size() * sizeof(int));
+    ds.grp_sub = (const int*)put(s.grp_sub.data(), s.grp_sub.size() * sizeof(int));
     t.stages.push_back(ds);
   }
   t.host = hs;

@@ -474,10 +474,21 @@ static ttn_block* make_block(ttn_ctx* ctx, const TreeInfo& tree, int n_states, c
 // ------------------------------------------------------------------------------------------------
 // C ABI helpers
 // ------------------------------------------------------------------------------------------------
+// Reports (once) a bounded device-side wait that gave up in work issued earlier on the context.
+static void raise_wait_timeout(ttn_ctx* ctx) {
+  if (!ctx || !ctx->h_wait) return;
+  volatile unsigned* f = ctx->h_wait;
+  if (*f == 0u) return;
+  *f = 0u;
+  TTN_FAIL(TTN_ETIMEOUT, "a bulk-copy barrier wait on the device gave up after 2 s; results of "
+                         "the work issued since the previous call are not valid");
+}
+
 template <class F>
 static ttn_status guarded(ttn_ctx* ctx, F&& f) {
   try {
     f();
+    raise_wait_timeout(ctx);
     if (ctx) ctx->last_error.clear();
     return TTN_OK;
   } catch (const TtnError& e) {
@@ -557,6 +568,13 @@ ttn_status ttn_create(ttn_ctx** out, int device, void* cuda_stream) {
       CUDA_CHECK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
       ctx->own_stream = true;
     }
+    void* hw = nullptr;
+    CUDA_CHECK(cudaHostAlloc(&hw, sizeof(unsigned), cudaHostAllocMapped));
+    ctx->h_wait = static_cast<unsigned*>(hw);
+    *ctx->h_wait = 0u;
+    void* dw = nullptr;
+    CUDA_CHECK(cudaHostGetDevicePointer(&dw, hw, 0));
+    ctx->d_wait = static_cast<unsigned*>(dw);
     cudaMemPool_t pool;
     CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, device));
     uint64_t thr = UINT64_MAX;
@@ -585,6 +603,7 @@ void ttn_destroy(ttn_ctx* ctx) {
   }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->h_wait) cudaFreeHost(ctx->h_wait);
   delete ctx;
 }
 

@@ -101,6 +101,10 @@ struct ttn_ctx {
   double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
   bool tf32x3 = false;           // float32 calls route level stages to tensor cores
   bool capturing = false;        // a CUDA graph is being captured on the stream (no events)
+  // Set (host-mapped) by a kernel whose bounded wait on a bulk-copy barrier gave up; read and
+  // cleared by the next entry point, which then returns TTN_ETIMEOUT.
+  unsigned* h_wait = nullptr;
+  unsigned* d_wait = nullptr;
 };
 
 // Sets ctx->tf32x3 for the duration of one entry-point call.
@@ -167,16 +171,22 @@ struct NodePlan {
 
 // Item tables of one GEMM stage: per item ("sub") the C offset and a CSR list of segments,
 // each with its own A and B offsets (device copy for the kernel, host copy for bounds checks).
+// Level stages also carry "A groups": lists of single-segment items that read the same A slice
+// (children of one prefix in the TTNO trie), so one staged A tile serves all of them.
 struct StageDev {
   int n_sub = 0;
   const long long* sub_c = nullptr;
   const int* seg_ptr = nullptr;
   const long long* seg_a = nullptr;
   const long long* seg_b = nullptr;
+  int n_grp = 0;                    // 0: no A groups (some item has several segments)
+  const int* grp_ptr = nullptr;     // CSR over grp_sub, n_grp + 1 entries
+  const int* grp_sub = nullptr;
 };
 struct StageHost {
   std::vector<long long> sub_c, seg_a, seg_b;
   std::vector<int> seg_ptr{0};
+  std::vector<int> grp_ptr{0}, grp_sub;
 };
 struct DevTables {
   DevBuf buf;   // all item tables of one (plan, dims) in one allocation
@@ -265,6 +275,7 @@ struct GemmDesc {
   const StageHost* hst;
   long long a_len, b_len, c_len;   // elements addressable from each base pointer
   int max_bra, max_ket;            // largest state index in pair_bra / pair_ket
+  unsigned* wait_flag;             // device view of ttn_ctx::h_wait (set by the launcher)
 };
 
 // A list of (bra, ket) pairs on the device plus the host facts the bounds checks need.
@@ -283,6 +294,9 @@ void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long
                         const T* term_coef, int max_w);
 // Specialised level-stage GEMM (a_sm = 1, N, K <= 64; items sum over their segments).
 bool level_shape_ok(const GemmDesc& g);
+// Largest A-group size the bulk-copy level kernel stages for an (M, N, K) float level stage
+// (0 when that kernel does not take the shape).
+int level_group_cap(int M, int N, int K);
 template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
 // Tensor-core (TF32 MMA, 3xTF32 split) level stage for float data, N <= 32, K <= 64.
 bool level_tc_ok(const GemmDesc& g);

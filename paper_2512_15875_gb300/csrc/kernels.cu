@@ -671,6 +671,331 @@ template void launch_combine_env<double>(ttn_ctx*, const double*, long long, lon
 template void launch_combine_env<float>(ttn_ctx*, const float*, long long, long long, float*,
                                         int, int, const int*, const int*, const float*, int);
 
+// ---- bulk copies (cp.async.bulk, the 1-D TMA path) completing on an mbarrier --------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Orders earlier generic-proxy accesses of shared memory before later bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase `parity` of the barrier; gives up after ~2 s of device time, raises the
+// context's wait flag and returns false (the caller then leaves the CTA without touching the
+// staged data).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned* flag) {
+  unsigned long long t0 = 0;
+  for (unsigned it = 0;; ++it) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255u) == 255u) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > 2000000000ull) {
+        if (flag) {
+          *reinterpret_cast<volatile unsigned*>(flag) = 1u;
+          __threadfence_system();
+        }
+        return false;
+      }
+    }
+  }
+}
+
+// Level stage with bulk-copied operands (float32): one CTA takes one row tile (rows_cta rows) of
+// one A group, i.e. up to sb_max single-segment items of one pair that read the same A slice.
+// The A tile (K rows of rows_cta contiguous floats) and each item's environment slice E[a][b]
+// (N x K contiguous) land in shared memory by bulk copies on one mbarrier; the slices are then
+// transposed in shared memory to Es[b][a]. Each thread owns 4 consecutive rows x NA/4 columns
+// of the output (a warp: 8 row groups x 4 column groups = 32 rows), reads its 4 rows of A with
+// one 16-byte shared load and its columns of E with 8-byte loads, and writes its outputs
+// straight to global memory (c_sm = N).
+template <int NA>
+__global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, int rows_cta,
+                                                        int sb_max, int vec_store) {
+  constexpr int CPT = NA / 4;
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long bar;
+  const int nk4 = (g.N * g.K + 3) & ~3;
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int q = (int)(rest % g.st.n_grp);
+  const int pair = (int)(rest / g.st.n_grp);
+  const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
+  const int r0 = rt * rows_cta;
+  const int nrow = min(rows_cta, g.M - r0);
+  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+  float* As = dsm;
+  float* Er = dsm + g.K * rows_cta;
+  float* Es = Er + sb_max * nk4;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float* Ab = Abase + g.st.seg_a[g.st.seg_ptr[g.st.grp_sub[gs]]] + r0;
+    mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
+    for (int b = 0; b < g.K; ++b)
+      bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
+    for (int j = 0; j < ns; ++j)
+      bulk_copy_g2s(Er + j * nk4, Bbase + g.st.seg_b[g.st.seg_ptr[g.st.grp_sub[gs + j]]],
+                    g.N * g.K * 4u, &bar);
+  }
+  const bool ok = mbar_wait(&bar, 0, g.wait_flag);
+  if (__syncthreads_or(!ok)) return;
+  for (int i = threadIdx.x; i < ns * g.K * NA; i += blockDim.x) {
+    const int j = i / (g.K * NA), rem = i - j * (g.K * NA);
+    const int b = rem / NA, a = rem - b * NA;
+    Es[i] = a < g.N ? Er[j * nk4 + a * g.K + b] : 0.f;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 2, cg = lane & 3;
+  const int rl = warp * 32 + rg * 4;
+  if (rl >= nrow) return;
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  float* Cpair = static_cast<float*>(g.C) + cidx * g.c_pstride;
+  for (int j = 0; j < ns; ++j) {
+    float acc[4][CPT];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) acc[i][c] = 0.f;
+    const float* es = Es + j * g.K * NA + cg * CPT;
+#pragma unroll 4
+    for (int b = 0; b < g.K; ++b) {
+      const float4 x4 = *reinterpret_cast<const float4*>(As + b * rows_cta + rl);
+      const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+      float e[CPT];
+#pragma unroll
+      for (int c = 0; c < CPT; c += 2) {
+        const float2 v = *reinterpret_cast<const float2*>(es + b * NA + c);
+        e[c] = v.x;
+        e[c + 1] = v.y;
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) acc[i][c] = fmaf(x[i], e[c], acc[i][c]);
+    }
+    float* dst = Cpair + g.st.sub_c[g.st.grp_sub[gs + j]] + (long long)(r0 + rl) * g.N + cg * CPT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (rl + i >= nrow) break;
+      if (vec_store) {
+#pragma unroll
+        for (int c = 0; c < CPT; c += 2)
+          *reinterpret_cast<float2*>(dst + (long long)i * g.N + c) =
+              make_float2(acc[i][c], acc[i][c + 1]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+          if (cg * CPT + c < g.N) dst[(long long)i * g.N + c] = acc[i][c];
+      }
+    }
+  }
+}
+
+
+// Level stage with bulk-copied operands for items that sum several segments (the segmented last
+// level of the operator-first order): Z[item] = sum_seg A_seg x E_seg. One CTA takes one row tile
+// of one item; each segment's A tile and E slice land in one stage of a two-stage ring of
+// mbarrier-tracked bulk copies (segment j + 2 is requested once segment j has been consumed), the
+// slice is transposed in shared memory, and the products accumulate in registers with the same
+// 4-row x NA/4-column thread tiles as level_tma_kernel.
+template <int NA>
+__global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtiles, int rows_cta,
+                                                            int vec_store) {
+  constexpr int CPT = NA / 4;
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  const int nk4 = (g.N * g.K + 3) & ~3;
+  const int stage = g.K * rows_cta + nk4 + g.K * NA;
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const int s0 = g.st.seg_ptr[sub], nseg = g.st.seg_ptr[sub + 1] - s0;
+  const int r0 = rt * rows_cta;
+  const int nrow = min(rows_cta, g.M - r0);
+  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+  auto issue = [&](int j, int st) {
+    float* As = dsm + st * stage;
+    float* Er = As + g.K * rows_cta;
+    const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
+    mbar_expect_tx(&bar[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
+    for (int b = 0; b < g.K; ++b)
+      bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &bar[st]);
+    bulk_copy_g2s(Er, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (nseg > 0) issue(0, 0);
+    if (nseg > 1) issue(1, 1);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rg = lane >> 2, cg = lane & 3;
+  const int rl = warp * 32 + rg * 4;
+  float acc[4][CPT];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[i][c] = 0.f;
+  unsigned phase[2] = {0u, 0u};
+  for (int j = 0; j < nseg; ++j) {
+    const int st = j & 1;
+    const bool ok = mbar_wait(&bar[st], phase[st], g.wait_flag);
+    phase[st] ^= 1u;
+    if (__syncthreads_or(!ok)) return;
+    const float* As = dsm + st * stage;
+    const float* Er = As + g.K * rows_cta;
+    float* Es = const_cast<float*>(Er) + nk4;
+    for (int i = threadIdx.x; i < g.K * NA; i += blockDim.x) {
+      const int b = i / NA, a = i - b * NA;
+      Es[i] = a < g.N ? Er[a * g.K + b] : 0.f;
+    }
+    __syncthreads();
+    if (rl < nrow) {
+      const float* es = Es + cg * CPT;
+#pragma unroll 4
+      for (int b = 0; b < g.K; ++b) {
+        const float4 x4 = *reinterpret_cast<const float4*>(As + b * rows_cta + rl);
+        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
+        float e[CPT];
+#pragma unroll
+        for (int c = 0; c < CPT; c += 2) {
+          const float2 v = *reinterpret_cast<const float2*>(es + b * NA + c);
+          e[c] = v.x;
+          e[c + 1] = v.y;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) acc[i][c] = fmaf(x[i], e[c], acc[i][c]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && j + 2 < nseg) {
+      fence_proxy_async();
+      issue(j + 2, st);
+    }
+  }
+  if (rl >= nrow) return;
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  float* dst = static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
+               (long long)(r0 + rl) * g.N + cg * CPT;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (rl + i >= nrow) break;
+    if (vec_store) {
+#pragma unroll
+      for (int c = 0; c < CPT; c += 2)
+        *reinterpret_cast<float2*>(dst + (long long)i * g.N + c) =
+            make_float2(acc[i][c], acc[i][c + 1]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CPT; ++c)
+        if (cg * CPT + c < g.N) dst[(long long)i * g.N + c] = acc[i][c];
+    }
+  }
+}
+
+namespace {
+int level_tma_na(int N) { return N <= 8 ? 8 : N <= 16 ? 16 : N <= 24 ? 24 : N <= 32 ? 32 : 0; }
+int level_tma_rows(int M) {
+  const int nwt = (M + 31) / 32;
+  const int ncta = (nwt + 8) / 9;
+  return (nwt + ncta - 1) / ncta * 32;
+}
+size_t level_tma_smem(int M, int N, int K, int sb) {
+  const int na = level_tma_na(N);
+  return sizeof(float) * ((size_t)K * level_tma_rows(M) + (size_t)sb * ((N * K + 3) & ~3) +
+                          (size_t)sb * K * na);
+}
+size_t level_tma_seg_smem(int M, int N, int K) {
+  const int na = level_tma_na(N);
+  return sizeof(float) * 2 *
+         ((size_t)K * level_tma_rows(M) + (size_t)((N * K + 3) & ~3) + (size_t)K * na);
+}
+constexpr size_t kLevelTmaSmem = 100 * 1024;
+}  // namespace
+
+int level_group_cap(int M, int N, int K) {
+  if (M <= 0 || M % 4 != 0 || K <= 0 || K > 64 || (N * K) % 4 != 0 || level_tma_na(N) == 0)
+    return 0;
+  for (int sb = 6; sb >= 1; --sb)
+    if (level_tma_smem(M, N, K, sb) <= kLevelTmaSmem) return sb;
+  return 0;
+}
+
+// True if a float32 level launch meets the bulk-copy kernel's layout and alignment needs: A rows
+// contiguous with a 16-byte aligned start for every (base, segment, k), E slices contiguous and
+// aligned, A groups present.
+static bool level_tma_ok(const GemmDesc& g) {
+  if (level_group_cap(g.M, g.N, g.K) <= 0) return false;
+  if (g.st.n_grp <= 0 && level_tma_seg_smem(g.M, g.N, g.K) > kLevelTmaSmem) return false;
+  if (g.a_sm != 1 || g.a_sk % 4 != 0 || g.b_sk != 1 || g.b_sn != g.K || g.c_sm != g.N ||
+      g.c_sn != 1)
+    return false;
+  if (g.A.pstride % 4 != 0 || g.B.pstride % 4 != 0) return false;
+  if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
+    return false;
+  for (long long a : g.hst->seg_a)
+    if (a % 4) return false;
+  for (long long b : g.hst->seg_b)
+    if (b % 4) return false;
+  return true;
+}
+
 template <class T>
 void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
@@ -680,6 +1005,74 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   }
   TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
   check_bounds(g, sizeof(T));
+  if (sizeof(T) == 4 && level_tma_ok(g) && g.st.n_grp == 0) {
+    // items with several segments: one CTA per (pair, item, row tile), segments through a ring
+    const int na = level_tma_na(g.N);
+    const int rows_cta = level_tma_rows(g.M);
+    const int rt = (g.M + rows_cta - 1) / rows_cta;
+    const size_t smem = level_tma_seg_smem(g.M, g.N, g.K);
+    bool vec = g.N == na && g.c_pstride % 2 == 0 &&
+               reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
+    for (long long c0 : g.hst->sub_c) vec = vec && c0 % 2 == 0;
+    const long long grid = (long long)rt * g.st.n_sub * g.n_pairs;
+    TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+    long long nseg = 0;
+    for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
+    const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
+    static const char* nm[] = {"level_tma_seg_f32_8", "level_tma_seg_f32_16",
+                               "level_tma_seg_f32_24", "level_tma_seg_f32_32"};
+    LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
+    GemmDesc gd = g;
+    gd.wait_flag = ctx->d_wait;
+    auto go = [&](auto kern) {
+      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kLevelTmaSmem));
+      kern<<<(unsigned)grid, rows_cta, smem, ctx->stream>>>(gd, rt, rows_cta, vec ? 1 : 0);
+    };
+    switch (na) {
+      case 8: go(level_tma_seg_kernel<8>); break;
+      case 16: go(level_tma_seg_kernel<16>); break;
+      case 24: go(level_tma_seg_kernel<24>); break;
+      default: go(level_tma_seg_kernel<32>); break;
+    }
+    CUDA_LAUNCH_CHECK();
+    return;
+  }
+  if (sizeof(T) == 4 && level_tma_ok(g)) {
+    const int na = level_tma_na(g.N);
+    const int rows_cta = level_tma_rows(g.M);
+    const int rt = (g.M + rows_cta - 1) / rows_cta;
+    int sb_max = 0;
+    for (int q = 0; q < g.st.n_grp; ++q)
+      sb_max = std::max(sb_max, g.hst->grp_ptr[q + 1] - g.hst->grp_ptr[q]);
+    const size_t smem = level_tma_smem(g.M, g.N, g.K, sb_max);
+    TTN_REQUIRE(smem <= kLevelTmaSmem, "level kernel: A group larger than its cap");
+    bool vec = g.N == na && g.c_pstride % 2 == 0 &&
+               reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
+    for (long long c0 : g.hst->sub_c) vec = vec && c0 % 2 == 0;
+    const long long grid = (long long)rt * g.st.n_grp * g.n_pairs;
+    TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+    const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
+    static const char* nm[] = {"level_tma_f32_8", "level_tma_f32_16", "level_tma_f32_24",
+                               "level_tma_f32_32"};
+    LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
+    GemmDesc gd = g;
+    gd.wait_flag = ctx->d_wait;
+    const int threads = rows_cta;   // 32 rows per warp
+    auto go = [&](auto kern) {
+      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kLevelTmaSmem));
+      kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0);
+    };
+    switch (na) {
+      case 8: go(level_tma_kernel<8>); break;
+      case 16: go(level_tma_kernel<16>); break;
+      case 24: go(level_tma_kernel<24>); break;
+      default: go(level_tma_kernel<32>); break;
+    }
+    CUDA_LAUNCH_CHECK();
+    return;
+  }
   const int rtiles = (g.M + kThreads - 1) / kThreads;
   const long long grid = (long long)rtiles * g.st.n_sub * g.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
@@ -788,6 +1181,147 @@ __global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
   }
 }
 
+
+// Closure GEMM with bulk-copied operands (float32): C[a][b] = sum_k A[a][k] Z[b][k] for one
+// item per CTA, M, N <= MP, NP. K is cut into chunks of kc_max (a multiple of 8) that land in
+// shared memory (rows padded to kc_max + 4 floats, so 16-byte loads of 8 consecutive rows hit
+// distinct banks) through a two-stage ring of mbarrier-tracked bulk copies; chunk c + 2 is in
+// flight while chunk c + 1 waits and chunk c is consumed. Each thread owns a TA x TB output tile
+// and one of NS interleaved k-slices; the slice partials are summed in a fixed order through
+// shared memory (aliasing the ring) at the end.
+template <int TA, int TB, int MP, int NP>
+__global__ void __launch_bounds__(kThreads, 3) closure_tma_kernel(GemmDesc g, int kc_max, int nstage) {
+  constexpr int NT = (MP / TA) * (NP / TB), NS = kThreads / NT;
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  const int ldk = kc_max + 4, stage = (MP + NP) * ldk;
+  const int sub = (int)(blockIdx.x % g.st.n_sub);
+  const int pair = (int)(blockIdx.x / g.st.n_sub);
+  const int seg = g.st.seg_ptr[sub];
+  const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
+  const float* Zb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
+  const int nchunk = (g.K + kc_max - 1) / kc_max;
+  auto issue = [&](int c, int s) {
+    const int k0 = c * kc_max, kc = min(kc_max, g.K - k0);
+    float* As = dsm + s * stage;
+    float* Zs = As + MP * ldk;
+    mbar_expect_tx(&bar[s], (unsigned)((g.M + g.N) * kc) * 4u);
+    for (int r = 0; r < g.M; ++r)
+      bulk_copy_g2s(As + r * ldk, Ab + (long long)r * g.a_sm + k0, kc * 4u, &bar[s]);
+    for (int r = 0; r < g.N; ++r)
+      bulk_copy_g2s(Zs + r * ldk, Zb + (long long)r * g.b_sn + k0, kc * 4u, &bar[s]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    issue(0, 0);
+    if (nchunk > 1) issue(1, 1);
+  }
+  const int tile = threadIdx.x % NT, ks = threadIdx.x / NT;
+  const int ti = tile / (NP / TB), tj = tile % (NP / TB);
+  float acc[TA][TB];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TB; ++j) acc[i][j] = 0.f;
+  unsigned phase[2] = {0u, 0u};
+  for (int c = 0; c < nchunk; ++c) {
+    const int s = nstage == 2 ? (c & 1) : 0;
+    const bool ok = mbar_wait(&bar[s], phase[s], g.wait_flag);
+    phase[s] ^= 1u;
+    if (__syncthreads_or(!ok)) return;
+    const int kc = min(kc_max, g.K - c * kc_max);
+    const float* As = dsm + s * stage;
+    const float* Zs = As + MP * ldk;
+    if (ks < NS) {
+      for (int qk = ks; qk < kc / 4; qk += NS) {
+        const int k = qk * 4;
+        float a[TA][4], b[TB][4];
+#pragma unroll
+        for (int i = 0; i < TA; ++i) load4(As + (ti * TA + i) * ldk + k, a[i]);
+#pragma unroll
+        for (int j = 0; j < TB; ++j) load4(Zs + (tj * TB + j) * ldk + k, b[j]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < TA; ++i)
+#pragma unroll
+            for (int j = 0; j < TB; ++j) acc[i][j] = fmaf(a[i][u], b[j][u], acc[i][j]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && c + nstage < nchunk) {
+      fence_proxy_async();
+      issue(c + nstage, s);
+    }
+  }
+  float* red = dsm;
+  if (ks < NS) {
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int j = 0; j < TB; ++j) red[(ks * MP + ti * TA + i) * NP + tj * TB + j] = acc[i][j];
+  }
+  __syncthreads();
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  float* Cb = static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
+  for (int i = threadIdx.x; i < MP * NP; i += kThreads) {
+    const int a = i / NP, b = i % NP;
+    if (a >= g.M || b >= g.N) continue;
+    float v = 0.f;
+    for (int q = 0; q < NS; ++q) v += red[q * MP * NP + i];
+    Cb[(long long)a * g.c_sm + (long long)b * g.c_sn] = v;
+  }
+}
+
+namespace {
+constexpr size_t kClosureTmaSmem = 200 * 1024;
+// chunk length (multiple of 8) and ring depth of the bulk-copy closure for contraction length K
+void closure_tma_chunks(int K, int& kc_max, int& nstage) {
+  if (K <= 256) {
+    kc_max = (K + 7) & ~7;
+    nstage = 1;
+  } else {
+    kc_max = 192;
+    nstage = 2;
+  }
+}
+int closure_tma_pad(const GemmDesc& g) {
+  const int mn = std::max(g.M, g.N);
+  return mn <= 12 ? 12 : mn <= 24 ? 24 : mn <= 32 ? 32 : 0;
+}
+size_t closure_tma_smem(int K, int pad) {
+  int kc_max, nstage;
+  closure_tma_chunks(K, kc_max, nstage);
+  const int nt = pad == 12 ? 16 : pad == 24 ? 16 : 32;
+  const size_t ring = (size_t)nstage * 2 * pad * (kc_max + 4);
+  const size_t red = (size_t)(kThreads / nt) * pad * pad;
+  return sizeof(float) * std::max(ring, red);
+}
+}  // namespace
+
+// True if a float32 closure launch meets the bulk-copy kernel's layout and alignment needs.
+static bool closure_tma_ok(const GemmDesc& g) {
+  const int pad = closure_tma_pad(g);
+  if (pad == 0 || g.K <= 0 || g.K % 4 != 0 || g.a_sk != 1 || g.b_sk != 1) return false;
+  if (g.a_sm % 4 != 0 || g.b_sn % 4 != 0 || g.A.pstride % 4 != 0 || g.B.pstride % 4 != 0)
+    return false;
+  if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
+    return false;
+  for (long long a : g.hst->seg_a)
+    if (a % 4) return false;
+  for (long long b : g.hst->seg_b)
+    if (b % 4) return false;
+  return closure_tma_smem(g.K, pad) <= kClosureTmaSmem;
+}
+
 bool closure_shape_ok(const GemmDesc& g) {
   if (g.a_sk != 1 || g.b_sk != 1 || g.M > 32 || g.N > 32) return false;
   for (int s = 0; s < g.st.n_sub; ++s)
@@ -804,6 +1338,25 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
   TTN_REQUIRE(grid <= 0x7fffffffLL, "closure grid too large");
   const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
   const double bytes = algorithmic_bytes(g, sizeof(T));
+  if (sizeof(T) == 4 && closure_tma_ok(g)) {
+    const int pad = closure_tma_pad(g);
+    int kc_max, nstage;
+    closure_tma_chunks(g.K, kc_max, nstage);
+    const size_t smem = closure_tma_smem(g.K, pad);
+    LaunchScope ls(ctx, "closure_tma_f32", flops, bytes);
+    GemmDesc gd = g;
+    gd.wait_flag = ctx->d_wait;
+    auto go = [&](auto kern) {
+      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kClosureTmaSmem));
+      kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(gd, kc_max, nstage);
+    };
+    if (pad == 12) go(closure_tma_kernel<3, 3, 12, 12>);
+    else if (pad == 24) go(closure_tma_kernel<6, 6, 24, 24>);
+    else go(closure_tma_kernel<4, 8, 32, 32>);
+    CUDA_LAUNCH_CHECK();
+    return;
+  }
   LaunchScope ls(ctx, sizeof(T) == 8 ? "closure_f64" : "closure_f32", flops, bytes);
   closure_kernel<T><<<grid, kThreads, 0, ctx->stream>>>(g);
   CUDA_LAUNCH_CHECK();
