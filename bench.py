@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gram-states", type=int, default=0,
+                    help="gram mode: states in the Gram (default 3n, the LOBPCG subspace); a "
+                         "smaller count gives the small case for counter captures")
     return ap.parse_args()
 
 
@@ -150,6 +153,12 @@ def roofline_of(prof, precision):
                else "fallback 6800 GB/s (of fallback)")
     if "f64" in name or name.startswith("jacobi"):
         alu, alu_src = FP64_PEAK_TFLOPS, "nominal GB300 FP64 1.25 TFLOP/s"
+    elif "tf32x3" in name:
+        # three TF32 tensor-core products per algorithmic multiply-add
+        bf16 = peaks.get("bf16_tflops", 1900.0)
+        alu = bf16 * (1100.0 / 2250.0) / 3.0
+        alu_src = (f"measured bf16 {bf16} TFLOP/s x nominal tf32/bf16 (1100/2250) / 3 products "
+                   f"({'of measured' if peaks else 'of fallback'})")
     else:
         alu, alu_src = FP32_PEAK_TFLOPS, "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)"
     # classic roofline: the kernel's algorithmic intensity against the machine balance decides
@@ -170,8 +179,41 @@ def roofline_of(prof, precision):
     rl["launches"] = rec["launches"]
     rl["avg_launch_ms"] = rec["ms"] / max(rec["launches"], 1)
     rl["share_of_timed_kernel_time"] = rec["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9)
-    rl["traffic"] = None
+    rl["traffic"], rl["traffic_source"] = measured_traffic(name, rec)
     return rl
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+
+
+def source_digest():
+    """Digest of the library sources; counters taken on other sources are not reused."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2512_15875_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.h"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(name, rec):
+    """DRAM bytes per launch of kernel `name`: the ratio of DRAM bytes (ncu) to the library's
+    algorithmic bytes over all launches of one captured Gram, times this run's algorithmic bytes
+    per launch. None when no capture exists for the current sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no capture"
+    text = open(TRAFFIC_FILE).read()
+    if "```json" not in text:
+        return None, "no capture"
+    d = json.loads(text.split("```json", 1)[1].split("```", 1)[0])
+    if d.get("source_digest") != source_digest():
+        return None, "capture taken on other sources"
+    k = d.get("kernels", {}).get(name)
+    if not k:
+        return None, "kernel not captured"
+    return (k["dram_bytes_per_algorithmic_byte"] * rec["bytes"] / max(rec["launches"], 1),
+            "profiles/dram_traffic.md")
 
 
 def aggregate_replicas(t, n_conv, dist, device="cpu"):
@@ -277,7 +319,8 @@ def gpu_arm(args, rank, world, local, dist):
         sblk = I.initial_block(w.tree, w.ham, w.bonds, 3 * n, seed=w.seed, noise=1e-2)
         bS = T.block_from_arrays(ctx, th, w.bonds, sblk)
         res = {}
-        for prec in ("fp32", "fp64"):
+        mixed = args.precision if args.precision != "fp64" else "fp32"
+        for prec in (mixed, "fp64"):
             T.ttn_synchronize(ctx)
             f0 = T.ttn_flop_count(ctx)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -295,7 +338,7 @@ def gram_arm(args, T, ctx, th, H, w, stream, local, dist):
     """Step = <s_k|H|s_l> and <s_k|s_l> over the 3n-state subspace (the LOBPCG Gram)."""
     import torch
     from paper_2512_15875_gb300 import inputs as I
-    n = 3 * w.n_states
+    n = args.gram_states or 3 * w.n_states
     sblk = I.initial_block(w.tree, w.ham, w.bonds, n, seed=w.seed, noise=1e-2)
     bS = T.block_from_arrays(ctx, th, w.bonds, sblk)
     for _ in range(args.warmup):
@@ -430,7 +473,7 @@ def main():
                           out["flops"] / t / 1e12, "unit": "TFLOP/s", "ms_per_step":
                           t * 1e3 / args.steps, "steps": args.steps, "dtype": args.precision,
                           "config": {"workload": f"{args.workload}: {w.description}",
-                                     "subspace": 3 * w.n_states},
+                                     "subspace": args.gram_states or 3 * w.n_states},
                           "roofline": rl, "clocks": out["clocks"],
                           "gpu_launches": out["launches"],
                           "kernels": {k: dict(v, share=v["ms"] / sum(x["ms"] for x in
@@ -463,10 +506,12 @@ def main():
     }
     if "gram" in out:
         g = out["gram"]
-        line["fp64_plain"] = {"gram_ms_fp32": g["fp32"]["ms"], "gram_ms_fp64": g["fp64"]["ms"],
-                              "gram_tflops_fp32": g["fp32"]["tflops"],
+        mixed = args.precision if args.precision != "fp64" else "fp32"
+        line["fp64_plain"] = {"mixed": mixed, "gram_ms_mixed": g[mixed]["ms"],
+                              "gram_ms_fp64": g["fp64"]["ms"],
+                              "gram_tflops_mixed": g[mixed]["tflops"],
                               "gram_tflops_fp64": g["fp64"]["tflops"],
-                              "speedup": g["fp64"]["ms"] / g["fp32"]["ms"]}
+                              "speedup": g["fp64"]["ms"] / g[mixed]["ms"]}
     if "e2e" in out:
         e = out["e2e"]
         line["e2e"] = {"value": e["n_conv"] * world / e["t"], "unit": UNIT,

@@ -735,75 +735,105 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   }
 }
 
-// Level stage with bulk-copied operands (float32): one CTA takes one row tile (rows_cta rows) of
-// one A group, i.e. up to sb_max single-segment items of one pair that read the same A slice.
-// The A tile (K rows of rows_cta contiguous floats) and each item's environment slice E[a][b]
-// (N x K contiguous) land in shared memory by bulk copies on one mbarrier; the slices are then
-// transposed in shared memory to Es[b][a]. Each thread owns 4 consecutive rows x NA/4 columns
-// of the output (a warp: 8 row groups x 4 column groups = 32 rows), reads its 4 rows of A with
-// one 16-byte shared load and its columns of E with 8-byte loads, and writes its outputs
-// straight to global memory (c_sm = N).
-template <int NA>
-__global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, int rows_cta,
-                                                        int sb_max, int vec_store) {
-  constexpr int CPT = NA / 4;
-  extern __shared__ __align__(16) float dsm[];
-  __shared__ __align__(8) unsigned long long bar;
-  const int nk4 = (g.N * g.K + 3) & ~3;
-  const long long bid = blockIdx.x;
-  const int rt = (int)(bid % rtiles);
-  const long long rest = bid / rtiles;
-  const int q = (int)(rest % g.st.n_grp);
-  const int pair = (int)(rest / g.st.n_grp);
-  const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
-  const int r0 = rt * rows_cta;
-  const int nrow = min(rows_cta, g.M - r0);
-  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
-  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
-  float* As = dsm;
-  float* Er = dsm + g.K * rows_cta;
-  float* Es = Er + sb_max * nk4;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_init_fence();
+// ---- level stage on bulk-copied tiles (float32 data) --------------------------------------------
+// out[r][a] = sum_b A[b][r] E[a][b] with the A tile (K rows of rows_cta contiguous floats, row
+// stride lda) and the environment slices E[a][b] (N x K contiguous) brought to shared memory by
+// bulk copies. A warp owns 32 rows of the tile and all NA (>= N, a multiple of 8) columns.
+//  * SIMT (TC = false): each thread owns 4 consecutive rows x NA/4 columns; the slice is
+//    transposed once to Es[b][a]; per b one 16-byte load of A, NA/8 8-byte loads of Es and
+//    4 * NA/4 FMAs. lda = rows_cta.
+//  * Tensor cores (TC = true, the TTN_TF32X3 precision): the warp's rows are two 16-row MMA
+//    tiles; mma.sync m16n8k8 TF32 with the 3xTF32 split x = hi + lo, hi = tf32(x),
+//    lo = tf32(x - hi), each product formed as lo*hi + hi*lo + hi*hi with float32 accumulation
+//    (relative error of a product ~2^-21 instead of ~2^-11 for plain TF32). The slice is split
+//    once into Eh/El[n][k] (row stride K + 4: conflict-free B fragments); A fragments are split
+//    on the fly. lda = rows_cta + 8 (conflict-free A fragments). Needs K % 8 == 0.
+// Fragment layout of m16n8k8 .row.col: groupID gq = lane / 4, tq = lane % 4; A: (gq, tq),
+// (gq + 8, tq), (gq, tq + 4), (gq + 8, tq + 4); B: (k = tq, n = gq), (k = tq + 4, n = gq);
+// C: (gq, 2tq), (gq, 2tq + 1), (gq + 8, 2tq), (gq + 8, 2tq + 1).
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_m16n8k8_tf32(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// floats of one staged environment slice in the compute layout
+template <int NA, bool TC>
+__host__ __device__ __forceinline__ int level_env_floats(int K) {
+  return TC ? 2 * NA * (K + 4) : K * NA;
+}
+
+// raw slice Er[a * K + b] (a < N) -> compute layout (padding columns zero); whole CTA
+template <int NA, bool TC>
+__device__ __forceinline__ void level_stage_env(const float* Er, float* Ec, int N, int K) {
+  if constexpr (TC) {
+    uint32_t* Eh = reinterpret_cast<uint32_t*>(Ec);
+    uint32_t* El = Eh + NA * (K + 4);
+    for (int i = threadIdx.x; i < NA * K; i += blockDim.x) {
+      const int n = i / K, k = i - n * K;
+      const float x = n < N ? Er[n * K + k] : 0.f;
+      const uint32_t hi = tf32_bits(x);
+      Eh[n * (K + 4) + k] = hi;
+      El[n * (K + 4) + k] = tf32_bits(x - __uint_as_float(hi));
+    }
+  } else {
+    for (int i = threadIdx.x; i < K * NA; i += blockDim.x) {
+      const int b = i / NA, a = i - b * NA;
+      Ec[i] = a < N ? Er[a * K + b] : 0.f;
+    }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const float* Ab = Abase + g.st.seg_a[g.st.seg_ptr[g.st.grp_sub[gs]]] + r0;
-    mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
-    for (int b = 0; b < g.K; ++b)
-      bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
-    for (int j = 0; j < ns; ++j)
-      bulk_copy_g2s(Er + j * nk4, Bbase + g.st.seg_b[g.st.seg_ptr[g.st.grp_sub[gs + j]]],
-                    g.N * g.K * 4u, &bar);
-  }
-  const bool ok = mbar_wait(&bar, 0, g.wait_flag);
-  if (__syncthreads_or(!ok)) return;
-  for (int i = threadIdx.x; i < ns * g.K * NA; i += blockDim.x) {
-    const int j = i / (g.K * NA), rem = i - j * (g.K * NA);
-    const int b = rem / NA, a = rem - b * NA;
-    Es[i] = a < g.N ? Er[j * nk4 + a * g.K + b] : 0.f;
-  }
-  __syncthreads();
+}
+
+// acc (NA floats per thread) += this warp's 32 rows of A x the staged slice
+template <int NA, bool TC>
+__device__ __forceinline__ void level_mac(const float* As, int lda, const float* Ec, int K,
+                                          float* acc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rg = lane >> 2, cg = lane & 3;
-  const int rl = warp * 32 + rg * 4;
-  if (rl >= nrow) return;
-  long long cidx = 0;
-  if (g.c_mode == MODE_PAIR) cidx = pair;
-  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
-  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
-  float* Cpair = static_cast<float*>(g.C) + cidx * g.c_pstride;
-  for (int j = 0; j < ns; ++j) {
-    float acc[4][CPT];
+  if constexpr (TC) {
+    constexpr int NT = NA / 8;
+    const uint32_t* Eh = reinterpret_cast<const uint32_t*>(Ec);
+    const uint32_t* El = Eh + NA * (K + 4);
+    const int gq = lane >> 2, tq = lane & 3, rw = warp * 32;
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      uint32_t ah[2][4], al[2][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int m = 0; m < 2; ++m) {
+        const float* ap = As + (k0 + tq) * lda + rw + m * 16 + gq;
+        const float x[4] = {ap[0], ap[8], ap[4 * lda], ap[4 * lda + 8]};
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) acc[i][c] = 0.f;
-    const float* es = Es + j * g.K * NA + cg * CPT;
+        for (int q = 0; q < 4; ++q) {
+          ah[m][q] = tf32_bits(x[q]);
+          al[m][q] = tf32_bits(x[q] - __uint_as_float(ah[m][q]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int off = (j * 8 + gq) * (K + 4) + k0 + tq;
+        const uint32_t bh[2] = {Eh[off], Eh[off + 4]};
+        const uint32_t bl[2] = {El[off], El[off + 4]};
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          float* d = acc + (m * NT + j) * 4;
+          mma_m16n8k8_tf32(d, al[m], bh);
+          mma_m16n8k8_tf32(d, ah[m], bl);
+          mma_m16n8k8_tf32(d, ah[m], bh);
+        }
+      }
+    }
+  } else {
+    constexpr int CPT = NA / 4;
+    const int rl = warp * 32 + (lane >> 2) * 4, cg = lane & 3;
+    const float* es = Ec + cg * CPT;
 #pragma unroll 4
-    for (int b = 0; b < g.K; ++b) {
-      const float4 x4 = *reinterpret_cast<const float4*>(As + b * rows_cta + rl);
+    for (int b = 0; b < K; ++b) {
+      const float4 x4 = *reinterpret_cast<const float4*>(As + b * lda + rl);
       const float x[4] = {x4.x, x4.y, x4.z, x4.w};
       float e[CPT];
 #pragma unroll
@@ -815,41 +845,129 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[i][c] = fmaf(x[i], e[c], acc[i][c]);
+        for (int c = 0; c < CPT; ++c) acc[i * CPT + c] = fmaf(x[i], e[c], acc[i * CPT + c]);
     }
-    float* dst = Cpair + g.st.sub_c[g.st.grp_sub[gs + j]] + (long long)(r0 + rl) * g.N + cg * CPT;
+  }
+}
+
+// rows [0, nrow) of the tile whose first row is at dst (row stride N)
+template <int NA, bool TC>
+__device__ __forceinline__ void level_store(float* dst, int nrow, int N, const float* acc,
+                                            int vec_store) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (TC) {
+    constexpr int NT = NA / 8;
+    const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = warp * 32 + m * 16 + gq + 8 * h;
+        if (r >= nrow) continue;
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const int col = j * 8 + 2 * tq;
+          const float* v = acc + (m * NT + j) * 4 + 2 * h;
+          float* o = dst + (long long)r * N + col;
+          if (vec_store) {
+            *reinterpret_cast<float2*>(o) = make_float2(v[0], v[1]);
+          } else {
+            if (col < N) o[0] = v[0];
+            if (col + 1 < N) o[1] = v[1];
+          }
+        }
+      }
+  } else {
+    constexpr int CPT = NA / 4;
+    const int rl = warp * 32 + (lane >> 2) * 4, cg = lane & 3;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       if (rl + i >= nrow) break;
+      float* o = dst + (long long)(rl + i) * N + cg * CPT;
       if (vec_store) {
 #pragma unroll
         for (int c = 0; c < CPT; c += 2)
-          *reinterpret_cast<float2*>(dst + (long long)i * g.N + c) =
-              make_float2(acc[i][c], acc[i][c + 1]);
+          *reinterpret_cast<float2*>(o + c) = make_float2(acc[i * CPT + c], acc[i * CPT + c + 1]);
       } else {
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
-          if (cg * CPT + c < g.N) dst[(long long)i * g.N + c] = acc[i][c];
+          if (cg * CPT + c < N) o[c] = acc[i * CPT + c];
       }
     }
   }
 }
 
+// One CTA takes one row tile of one A group, i.e. up to sb_max single-segment items of one
+// pair that read the same A slice: the A tile and every item's slice land on one mbarrier, each
+// slice is brought to the compute layout, and the items are computed one after the other from
+// the one staged tile.
+template <int NA, bool TC>
+__global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, int rows_cta,
+                                                        int sb_max, int vec_store) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long bar;
+  const int lda = TC ? rows_cta + 8 : rows_cta;
+  const int nk4 = (g.N * g.K + 3) & ~3;
+  const int esz = level_env_floats<NA, TC>(g.K);
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int q = (int)(rest % g.st.n_grp);
+  const int pair = (int)(rest / g.st.n_grp);
+  const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
+  const int r0 = rt * rows_cta;
+  const int nrow = min(rows_cta, g.M - r0);
+  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+  float* As = dsm;
+  float* Er = dsm + g.K * lda;
+  float* Ec = Er + sb_max * nk4;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float* Ab = Abase + g.st.seg_a[g.st.seg_ptr[g.st.grp_sub[gs]]] + r0;
+    mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
+    for (int b = 0; b < g.K; ++b)
+      bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
+    for (int j = 0; j < ns; ++j)
+      bulk_copy_g2s(Er + j * nk4, Bbase + g.st.seg_b[g.st.seg_ptr[g.st.grp_sub[gs + j]]],
+                    g.N * g.K * 4u, &bar);
+  }
+  const bool ok = mbar_wait(&bar, 0, g.wait_flag);
+  if (__syncthreads_or(!ok)) return;
+  for (int j = 0; j < ns; ++j) level_stage_env<NA, TC>(Er + j * nk4, Ec + j * esz, g.N, g.K);
+  __syncthreads();
+  if ((threadIdx.x >> 5) * 32 >= nrow) return;   // whole warps only (MMA needs all lanes)
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  float* Cpair = static_cast<float*>(g.C) + cidx * g.c_pstride;
+  for (int j = 0; j < ns; ++j) {
+    float acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+    level_mac<NA, TC>(As, lda, Ec + j * esz, g.K, acc);
+    level_store<NA, TC>(Cpair + g.st.sub_c[g.st.grp_sub[gs + j]] + (long long)r0 * g.N, nrow,
+                        g.N, acc, vec_store);
+  }
+}
 
-// Level stage with bulk-copied operands for items that sum several segments (the segmented last
-// level of the operator-first order): Z[item] = sum_seg A_seg x E_seg. One CTA takes one row tile
-// of one item; each segment's A tile and E slice land in one stage of a two-stage ring of
-// mbarrier-tracked bulk copies (segment j + 2 is requested once segment j has been consumed), the
-// slice is transposed in shared memory, and the products accumulate in registers with the same
-// 4-row x NA/4-column thread tiles as level_tma_kernel.
-template <int NA>
+// Items that sum several segments (the segmented last level of the operator-first order):
+// Z[item] = sum_seg A_seg x E_seg. One CTA takes one row tile of one item; each segment's A tile
+// and slice land in one stage of a two-stage ring of mbarrier-tracked bulk copies (segment j + 2
+// is requested once segment j has been consumed) and accumulate in registers.
+template <int NA, bool TC>
 __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtiles, int rows_cta,
                                                             int vec_store) {
-  constexpr int CPT = NA / 4;
   extern __shared__ __align__(16) float dsm[];
   __shared__ __align__(8) unsigned long long bar[2];
+  const int lda = TC ? rows_cta + 8 : rows_cta;
   const int nk4 = (g.N * g.K + 3) & ~3;
-  const int stage = g.K * rows_cta + nk4 + g.K * NA;
+  const int stage = g.K * lda + nk4 + level_env_floats<NA, TC>(g.K);
   const long long bid = blockIdx.x;
   const int rt = (int)(bid % rtiles);
   const long long rest = bid / rtiles;
@@ -862,11 +980,11 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
   const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
   auto issue = [&](int j, int st) {
     float* As = dsm + st * stage;
-    float* Er = As + g.K * rows_cta;
+    float* Er = As + g.K * lda;
     const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
     mbar_expect_tx(&bar[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
     for (int b = 0; b < g.K; ++b)
-      bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &bar[st]);
+      bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &bar[st]);
     bulk_copy_g2s(Er, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &bar[st]);
   };
   if (threadIdx.x == 0) {
@@ -879,14 +997,10 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
     if (nseg > 0) issue(0, 0);
     if (nseg > 1) issue(1, 1);
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rg = lane >> 2, cg = lane & 3;
-  const int rl = warp * 32 + rg * 4;
-  float acc[4][CPT];
+  const bool live = (threadIdx.x >> 5) * 32 < nrow;   // warp-uniform
+  float acc[NA];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[i][c] = 0.f;
+  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
   unsigned phase[2] = {0u, 0u};
   for (int j = 0; j < nseg; ++j) {
     const int st = j & 1;
@@ -894,59 +1008,25 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
     phase[st] ^= 1u;
     if (__syncthreads_or(!ok)) return;
     const float* As = dsm + st * stage;
-    const float* Er = As + g.K * rows_cta;
-    float* Es = const_cast<float*>(Er) + nk4;
-    for (int i = threadIdx.x; i < g.K * NA; i += blockDim.x) {
-      const int b = i / NA, a = i - b * NA;
-      Es[i] = a < g.N ? Er[a * g.K + b] : 0.f;
-    }
+    const float* Er = As + g.K * lda;
+    float* Ec = const_cast<float*>(Er) + nk4;
+    level_stage_env<NA, TC>(Er, Ec, g.N, g.K);
     __syncthreads();
-    if (rl < nrow) {
-      const float* es = Es + cg * CPT;
-#pragma unroll 4
-      for (int b = 0; b < g.K; ++b) {
-        const float4 x4 = *reinterpret_cast<const float4*>(As + b * rows_cta + rl);
-        const float x[4] = {x4.x, x4.y, x4.z, x4.w};
-        float e[CPT];
-#pragma unroll
-        for (int c = 0; c < CPT; c += 2) {
-          const float2 v = *reinterpret_cast<const float2*>(es + b * NA + c);
-          e[c] = v.x;
-          e[c + 1] = v.y;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int c = 0; c < CPT; ++c) acc[i][c] = fmaf(x[i], e[c], acc[i][c]);
-      }
-    }
+    if (live) level_mac<NA, TC>(As, lda, Ec, g.K, acc);
     __syncthreads();
     if (threadIdx.x == 0 && j + 2 < nseg) {
       fence_proxy_async();
       issue(j + 2, st);
     }
   }
-  if (rl >= nrow) return;
+  if (!live) return;
   long long cidx = 0;
   if (g.c_mode == MODE_PAIR) cidx = pair;
   else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
   else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
-  float* dst = static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
-               (long long)(r0 + rl) * g.N + cg * CPT;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    if (rl + i >= nrow) break;
-    if (vec_store) {
-#pragma unroll
-      for (int c = 0; c < CPT; c += 2)
-        *reinterpret_cast<float2*>(dst + (long long)i * g.N + c) =
-            make_float2(acc[i][c], acc[i][c + 1]);
-    } else {
-#pragma unroll
-      for (int c = 0; c < CPT; ++c)
-        if (cg * CPT + c < g.N) dst[(long long)i * g.N + c] = acc[i][c];
-    }
-  }
+  level_store<NA, TC>(static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
+                          (long long)r0 * g.N,
+                      nrow, g.N, acc, vec_store);
 }
 
 namespace {
@@ -956,24 +1036,28 @@ int level_tma_rows(int M) {
   const int ncta = (nwt + 8) / 9;
   return (nwt + ncta - 1) / ncta * 32;
 }
-size_t level_tma_smem(int M, int N, int K, int sb) {
+int level_env_floats_host(int NA, bool tc, int K) { return tc ? 2 * NA * (K + 4) : K * NA; }
+size_t level_tma_smem(int M, int N, int K, int sb, bool tc) {
   const int na = level_tma_na(N);
-  return sizeof(float) * ((size_t)K * level_tma_rows(M) + (size_t)sb * ((N * K + 3) & ~3) +
-                          (size_t)sb * K * na);
+  const int lda = level_tma_rows(M) + (tc ? 8 : 0);
+  return sizeof(float) * ((size_t)K * lda + (size_t)sb * ((N * K + 3) & ~3) +
+                          (size_t)sb * level_env_floats_host(na, tc, K));
 }
-size_t level_tma_seg_smem(int M, int N, int K) {
+size_t level_tma_seg_smem(int M, int N, int K, bool tc) {
   const int na = level_tma_na(N);
+  const int lda = level_tma_rows(M) + (tc ? 8 : 0);
   return sizeof(float) * 2 *
-         ((size_t)K * level_tma_rows(M) + (size_t)((N * K + 3) & ~3) + (size_t)K * na);
+         ((size_t)K * lda + (size_t)((N * K + 3) & ~3) + (size_t)level_env_floats_host(na, tc, K));
 }
 constexpr size_t kLevelTmaSmem = 100 * 1024;
 }  // namespace
 
+// The cap holds for both compute layouts (the tensor-core layout is the larger one).
 int level_group_cap(int M, int N, int K) {
   if (M <= 0 || M % 4 != 0 || K <= 0 || K > 64 || (N * K) % 4 != 0 || level_tma_na(N) == 0)
     return 0;
   for (int sb = 6; sb >= 1; --sb)
-    if (level_tma_smem(M, N, K, sb) <= kLevelTmaSmem) return sb;
+    if (level_tma_smem(M, N, K, sb, true) <= kLevelTmaSmem) return sb;
   return 0;
 }
 
@@ -982,7 +1066,7 @@ int level_group_cap(int M, int N, int K) {
 // aligned, A groups present.
 static bool level_tma_ok(const GemmDesc& g) {
   if (level_group_cap(g.M, g.N, g.K) <= 0) return false;
-  if (g.st.n_grp <= 0 && level_tma_seg_smem(g.M, g.N, g.K) > kLevelTmaSmem) return false;
+  if (g.st.n_grp <= 0 && level_tma_seg_smem(g.M, g.N, g.K, true) > kLevelTmaSmem) return false;
   if (g.a_sm != 1 || g.a_sk % 4 != 0 || g.b_sk != 1 || g.b_sn != g.K || g.c_sm != g.N ||
       g.c_sn != 1)
     return false;
@@ -999,18 +1083,20 @@ static bool level_tma_ok(const GemmDesc& g) {
 template <class T>
 void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
-  if (sizeof(T) == 4 && ctx->tf32x3 && level_tc_ok(g)) {
+  TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
+  check_bounds(g, sizeof(T));
+  // TTN_TF32X3: tensor-core compute on the staged tiles (K a multiple of 8)
+  const bool tc = sizeof(T) == 4 && ctx->tf32x3 && g.K % 8 == 0;
+  if (sizeof(T) == 4 && ctx->tf32x3 && !(tc && level_tma_ok(g)) && level_tc_ok(g)) {
     launch_level_tc(ctx, g);
     return;
   }
-  TTN_REQUIRE(level_shape_ok(g), "level kernel: unsupported shape");
-  check_bounds(g, sizeof(T));
   if (sizeof(T) == 4 && level_tma_ok(g) && g.st.n_grp == 0) {
     // items with several segments: one CTA per (pair, item, row tile), segments through a ring
     const int na = level_tma_na(g.N);
     const int rows_cta = level_tma_rows(g.M);
     const int rt = (g.M + rows_cta - 1) / rows_cta;
-    const size_t smem = level_tma_seg_smem(g.M, g.N, g.K);
+    const size_t smem = level_tma_seg_smem(g.M, g.N, g.K, tc);
     bool vec = g.N == na && g.c_pstride % 2 == 0 &&
                reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
     for (long long c0 : g.hst->sub_c) vec = vec && c0 % 2 == 0;
@@ -1021,7 +1107,9 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
     static const char* nm[] = {"level_tma_seg_f32_8", "level_tma_seg_f32_16",
                                "level_tma_seg_f32_24", "level_tma_seg_f32_32"};
-    LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
+    static const char* nm_tc[] = {"level_tma_seg_tf32x3_8", "level_tma_seg_tf32x3_16",
+                                  "level_tma_seg_tf32x3_24", "level_tma_seg_tf32x3_32"};
+    LaunchScope ls(ctx, (tc ? nm_tc : nm)[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
     auto go = [&](auto kern) {
@@ -1029,11 +1117,20 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
                                       (int)kLevelTmaSmem));
       kern<<<(unsigned)grid, rows_cta, smem, ctx->stream>>>(gd, rt, rows_cta, vec ? 1 : 0);
     };
-    switch (na) {
-      case 8: go(level_tma_seg_kernel<8>); break;
-      case 16: go(level_tma_seg_kernel<16>); break;
-      case 24: go(level_tma_seg_kernel<24>); break;
-      default: go(level_tma_seg_kernel<32>); break;
+    if (tc) {
+      switch (na) {
+        case 8: go(level_tma_seg_kernel<8, true>); break;
+        case 16: go(level_tma_seg_kernel<16, true>); break;
+        case 24: go(level_tma_seg_kernel<24, true>); break;
+        default: go(level_tma_seg_kernel<32, true>); break;
+      }
+    } else {
+      switch (na) {
+        case 8: go(level_tma_seg_kernel<8, false>); break;
+        case 16: go(level_tma_seg_kernel<16, false>); break;
+        case 24: go(level_tma_seg_kernel<24, false>); break;
+        default: go(level_tma_seg_kernel<32, false>); break;
+      }
     }
     CUDA_LAUNCH_CHECK();
     return;
@@ -1045,7 +1142,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     int sb_max = 0;
     for (int q = 0; q < g.st.n_grp; ++q)
       sb_max = std::max(sb_max, g.hst->grp_ptr[q + 1] - g.hst->grp_ptr[q]);
-    const size_t smem = level_tma_smem(g.M, g.N, g.K, sb_max);
+    const size_t smem = level_tma_smem(g.M, g.N, g.K, sb_max, tc);
     TTN_REQUIRE(smem <= kLevelTmaSmem, "level kernel: A group larger than its cap");
     bool vec = g.N == na && g.c_pstride % 2 == 0 &&
                reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
@@ -1055,7 +1152,9 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
     static const char* nm[] = {"level_tma_f32_8", "level_tma_f32_16", "level_tma_f32_24",
                                "level_tma_f32_32"};
-    LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
+    static const char* nm_tc[] = {"level_tma_tf32x3_8", "level_tma_tf32x3_16",
+                                  "level_tma_tf32x3_24", "level_tma_tf32x3_32"};
+    LaunchScope ls(ctx, (tc ? nm_tc : nm)[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
     const int threads = rows_cta;   // 32 rows per warp
@@ -1064,11 +1163,20 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
                                       (int)kLevelTmaSmem));
       kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0);
     };
-    switch (na) {
-      case 8: go(level_tma_kernel<8>); break;
-      case 16: go(level_tma_kernel<16>); break;
-      case 24: go(level_tma_kernel<24>); break;
-      default: go(level_tma_kernel<32>); break;
+    if (tc) {
+      switch (na) {
+        case 8: go(level_tma_kernel<8, true>); break;
+        case 16: go(level_tma_kernel<16, true>); break;
+        case 24: go(level_tma_kernel<24, true>); break;
+        default: go(level_tma_kernel<32, true>); break;
+      }
+    } else {
+      switch (na) {
+        case 8: go(level_tma_kernel<8, false>); break;
+        case 16: go(level_tma_kernel<16, false>); break;
+        case 24: go(level_tma_kernel<24, false>); break;
+        default: go(level_tma_kernel<32, false>); break;
+      }
     }
     CUDA_LAUNCH_CHECK();
     return;
