@@ -1430,6 +1430,88 @@ static bool closure_tma_ok(const GemmDesc& g) {
   return closure_tma_smem(g.K, pad) <= kClosureTmaSmem;
 }
 
+
+// Closure GEMM for short contractions (K <= 256) whose rows the bulk-copy kernel cannot take
+// (K or the row starts not multiples of 4 floats, e.g. K = 81 or 9 on the chain nodes): both
+// operand blocks (M x K and N x K) are loaded with coalesced element loads into shared rows of
+// odd stride (conflict-free scalar loads of 8 rows of a tile), then TA x TB register tiles x NS
+// interleaved k-slices as in closure_tma_kernel, slice partials summed in a fixed order.
+template <class T, int TA, int TB, int MP, int NP>
+__global__ void __launch_bounds__(kThreads, 3) closure_small_kernel(GemmDesc g, int ldk) {
+  constexpr int NT = (MP / TA) * (NP / TB), NS = kThreads / NT;
+  extern __shared__ __align__(16) unsigned char dsm_raw[];
+  T* As = reinterpret_cast<T*>(dsm_raw);
+  T* Zs = As + MP * ldk;
+  const int sub = (int)(blockIdx.x % g.st.n_sub);
+  const int pair = (int)(blockIdx.x / g.st.n_sub);
+  const int seg = g.st.seg_ptr[sub];
+  const T* Ab = operand_base<T>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
+  const T* Zb = operand_base<T>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
+  for (int i = threadIdx.x; i < g.M * g.K; i += kThreads) {
+    const int r = i / g.K, k = i - r * g.K;
+    As[r * ldk + k] = Ab[(long long)r * g.a_sm + k];
+  }
+  for (int i = threadIdx.x; i < g.N * g.K; i += kThreads) {
+    const int r = i / g.K, k = i - r * g.K;
+    Zs[r * ldk + k] = Zb[(long long)r * g.b_sn + k];
+  }
+  __syncthreads();
+  const int tile = threadIdx.x % NT, ks = threadIdx.x / NT;
+  const int ti = tile / (NP / TB), tj = tile % (NP / TB);
+  T acc[TA][TB];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TB; ++j) acc[i][j] = T(0);
+  if (ks < NS) {
+    // rows past M / N hold stale shared memory; they only reach accumulators that are dropped
+    for (int k = ks; k < g.K; k += NS) {
+      T a[TA], b[TB];
+#pragma unroll
+      for (int i = 0; i < TA; ++i) a[i] = As[(ti * TA + i) * ldk + k];
+#pragma unroll
+      for (int j = 0; j < TB; ++j) b[j] = Zs[(tj * TB + j) * ldk + k];
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = 0; j < TB; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+  }
+  __syncthreads();
+  T* red = As;
+  if (ks < NS) {
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int j = 0; j < TB; ++j) red[(ks * MP + ti * TA + i) * NP + tj * TB + j] = acc[i][j];
+  }
+  __syncthreads();
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  T* Cb = static_cast<T*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub];
+  for (int i = threadIdx.x; i < MP * NP; i += kThreads) {
+    const int a = i / NP, b = i % NP;
+    if (a >= g.M || b >= g.N) continue;
+    T v = T(0);
+    for (int q = 0; q < NS; ++q) v += red[q * MP * NP + i];
+    Cb[(long long)a * g.c_sm + (long long)b * g.c_sn] = v;
+  }
+}
+
+namespace {
+// shared bytes of closure_small_kernel: the two operand blocks, or the slice partials
+size_t closure_small_smem(int K, int pad, size_t elem) {
+  const int ldk = K | 1;
+  const int nt = pad == 12 ? 16 : pad == 24 ? 16 : 32;
+  const size_t ops = (size_t)2 * pad * ldk;
+  const size_t red = (size_t)(kThreads / nt) * pad * pad;
+  return elem * std::max(ops, red);
+}
+constexpr size_t kClosureSmallSmem = 96 * 1024;
+}  // namespace
+
 bool closure_shape_ok(const GemmDesc& g) {
   if (g.a_sk != 1 || g.b_sk != 1 || g.M > 32 || g.N > 32) return false;
   for (int s = 0; s < g.st.n_sub; ++s)
@@ -1446,6 +1528,23 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
   TTN_REQUIRE(grid <= 0x7fffffffLL, "closure grid too large");
   const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
   const double bytes = algorithmic_bytes(g, sizeof(T));
+  const int pad_small = closure_tma_pad(g);
+  if (sizeof(T) == 4 && !closure_tma_ok(g) && pad_small > 0 && g.K <= 256 &&
+      closure_small_smem(g.K, pad_small, sizeof(T)) <= kClosureSmallSmem) {
+    const int ldk = g.K | 1;
+    const size_t smem = closure_small_smem(g.K, pad_small, sizeof(T));
+    LaunchScope ls(ctx, "closure_small_f32", flops, bytes);
+    auto go = [&](auto kern) {
+      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kClosureSmallSmem));
+      kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(g, ldk);
+    };
+    if (pad_small == 12) go(closure_small_kernel<float, 3, 3, 12, 12>);
+    else if (pad_small == 24) go(closure_small_kernel<float, 6, 6, 24, 24>);
+    else go(closure_small_kernel<float, 4, 8, 32, 32>);
+    CUDA_LAUNCH_CHECK();
+    return;
+  }
   if (sizeof(T) == 4 && closure_tma_ok(g)) {
     const int pad = closure_tma_pad(g);
     int kc_max, nstage;
