@@ -56,14 +56,27 @@ __device__ T block_sum(T v, T* red) {
   return red[32];
 }
 
-// Householder QR of one rows x D matrix per CTA (row-major, rows >= D): A is overwritten by the
-// reflectors, Q (rows x D) and R (D x D, non-negative diagonal) are written out.
+// Householder QR of one rows x D matrix per CTA (row-major, rows >= D): the reflectors
+// overwrite the working copy of A, Q (rows x D) and R (D x D, non-negative diagonal) are written
+// out. With in_smem the working copies of A and Q live in dynamic shared memory (2 rows D
+// elements), so the column passes read and write on chip; A in global memory is then left as
+// it was.
 template <class T>
-__global__ void __launch_bounds__(kT) householder_qr_kernel(T* __restrict__ A, T* __restrict__ Q,
+__global__ void __launch_bounds__(kT) householder_qr_kernel(T* __restrict__ A_g,
+                                                           T* __restrict__ Q_g,
                                                            T* __restrict__ R, int rows, int D,
-                                                           long long mstride) {
-  A += (long long)blockIdx.x * mstride;
-  Q += (long long)blockIdx.x * mstride;
+                                                           long long mstride, int in_smem) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  T* A = A_g + (long long)blockIdx.x * mstride;
+  T* Q = Q_g + (long long)blockIdx.x * mstride;
+  T* const Q_out = Q;
+  if (in_smem) {
+    T* As = reinterpret_cast<T*>(qr_smem);
+    for (long long i = threadIdx.x; i < (long long)rows * D; i += blockDim.x) As[i] = A[i];
+    A = As;
+    Q = As + (long long)rows * D;
+    __syncthreads();
+  }
   R += (long long)blockIdx.x * D * D;
   __shared__ T red[33];
   __shared__ T tau[64];
@@ -161,6 +174,10 @@ __global__ void __launch_bounds__(kT) householder_qr_kernel(T* __restrict__ A, T
           -Q[(long long)i * D + j];
     }
     __syncthreads();
+  }
+  if (in_smem) {
+    __syncthreads();
+    for (long long i = threadIdx.x; i < (long long)rows * D; i += blockDim.x) Q_out[i] = Q[i];
   }
 }
 
@@ -834,8 +851,14 @@ static void qr_move(ttn_ctx* ctx, ttn_block* b, int u, int v) {
   {
     LaunchScope ls(ctx, sizeof(T) == 8 ? "householder_qr_f64" : "householder_qr_f32",
                    4.0 * rows * D * D * n, 4.0 * sizeof(T) * size * n);
-    householder_qr_kernel<T><<<n, kT, 0, st>>>(M.as<T>(), Q.as<T>(), R.as<T>(), (int)rows, D,
-                                               size);
+    // working copies on chip when both fit (c2 backbone: 576 x 24 float32 = 55 KB each)
+    const size_t smem = 2 * (size_t)rows * D * sizeof(T);
+    const bool on_chip = smem <= 200 * 1024;
+    if (on_chip)
+      CUDA_CHECK(cudaFuncSetAttribute(householder_qr_kernel<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    householder_qr_kernel<T><<<n, kT, on_chip ? smem : 0, st>>>(
+        M.as<T>(), Q.as<T>(), R.as<T>(), (int)rows, D, size, on_chip ? 1 : 0);
     CUDA_LAUNCH_CHECK();
   }
   std::vector<int> pdims(nl + 1), inv(nl + 1);
