@@ -385,7 +385,7 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     int max_w = 0;
     for (int x : p.fT_w) max_w = std::max(max_w, x);
     const void* coef = sizeof(T) == 8 ? p.d_fT_coef64.p : p.d_fT_coef32.p;
-    launch_combine_env<T>(ctx, env[c], (long long)Dw[c] * eslice, eslice, Et.as<T>(), P, nG,
+    launch_combine_env<T>(ctx, env[c], (long long)Dw[c] * eslice, Da[c], Db[c], Et.as<T>(), P, nG,
                           p.d_fG_term_ptr.as<int>(), p.d_fT_w.as<int>(),
                           static_cast<const T*>(coef), max_w);
     GemmDesc g{};
@@ -395,8 +395,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.K = Db[c];
     g.a_sm = 1;
     g.a_sk = rest;
-    g.b_sn = Db[c];
-    g.b_sk = 1;
+    g.b_sn = 1;          // Et slices are stored [b][a]
+    g.b_sk = Da[c];
     g.c_sm = Da[c];
     g.c_sn = 1;
     g.A = {prev, prev_mode, prev_pstride};

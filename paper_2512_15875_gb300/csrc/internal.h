@@ -287,9 +287,10 @@ struct PairSet {
 };
 
 template <class T> void launch_gemm(ttn_ctx* ctx, const GemmDesc& g);
-// Et[pair][G] = sum_{t in G} coef_t E[pair][w_t] (operator-first fold of a d = 1 node).
+// Et[pair][G] = sum_{t in G} coef_t E[pair][w_t] (operator-first fold of a d = 1 node); the
+// da x db slices [a][b] of E are written transposed ([b][a]) into Et.
 template <class T>
-void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long eslice, T* Et,
+void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, int da, int db, T* Et,
                         int n_pairs, int nG, const int* term_ptr, const int* term_w,
                         const T* term_coef, int max_w);
 // Specialised level-stage GEMM (a_sm = 1, N, K <= 64; items sum over their segments).

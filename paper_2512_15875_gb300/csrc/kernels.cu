@@ -629,19 +629,24 @@ bool level_shape_ok(const GemmDesc& g) {
   return g.a_sm == 1 && g.c_sn == 1 && g.c_sm == g.N && g.K <= 64 && g.N <= 64;
 }
 
+// Et[pair][G] = sum_{t in G} coef_t E[pair][w_t], written transposed: E slices are [a][b]
+// (da x db), Et slices [b][a], so the segmented level stage that consumes Et can take each
+// slice into shared memory as it lands (the layout its thread tiles read).
 template <class T>
-__global__ void combine_env_kernel(const T* __restrict__ E, long long e_pstride,
-                                   long long eslice, T* __restrict__ Et, int nG,
-                                   const int* __restrict__ term_ptr, const int* __restrict__ term_w,
+__global__ void combine_env_kernel(const T* __restrict__ E, long long e_pstride, int da, int db,
+                                   T* __restrict__ Et, int nG, const int* __restrict__ term_ptr,
+                                   const int* __restrict__ term_w,
                                    const T* __restrict__ term_coef, long long total) {
+  const long long eslice = (long long)da * db;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long per_pair = (long long)nG * eslice;
     const long long pair = idx / per_pair;
     const long long r = idx - pair * per_pair;
     const int G = (int)(r / eslice);
-    const long long e = r - (long long)G * eslice;
-    const T* Ep = E + pair * e_pstride + e;
+    const int e_t = (int)(r - (long long)G * eslice);   // b * da + a
+    const int b = e_t / da, a = e_t - b * da;
+    const T* Ep = E + pair * e_pstride + (long long)a * db + b;
     T acc = T(0);
     for (int t = term_ptr[G]; t < term_ptr[G + 1]; ++t)
       acc = fma(term_coef[t], Ep[(long long)term_w[t] * eslice], acc);
@@ -650,9 +655,10 @@ __global__ void combine_env_kernel(const T* __restrict__ E, long long e_pstride,
 }
 
 template <class T>
-void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long eslice, T* Et,
+void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, int da, int db, T* Et,
                         int n_pairs, int nG, const int* term_ptr, const int* term_w,
                         const T* term_coef, int max_w) {
+  const long long eslice = (long long)da * db;
   const long long total = (long long)n_pairs * nG * eslice;
   if (total == 0) return;
   TTN_REQUIRE((long long)(max_w + 1) * eslice <= e_pstride, "combine bounds");
@@ -660,15 +666,15 @@ void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, long long
                  sizeof(T) * 2.0 * total);
   long long blocks = (total + kThreads - 1) / kThreads;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  combine_env_kernel<T><<<(int)blocks, kThreads, 0, ctx->stream>>>(E, e_pstride, eslice, Et, nG,
+  combine_env_kernel<T><<<(int)blocks, kThreads, 0, ctx->stream>>>(E, e_pstride, da, db, Et, nG,
                                                                  term_ptr, term_w, term_coef,
                                                                  total);
   CUDA_LAUNCH_CHECK();
 }
 
-template void launch_combine_env<double>(ttn_ctx*, const double*, long long, long long, double*,
+template void launch_combine_env<double>(ttn_ctx*, const double*, long long, int, int, double*,
                                          int, int, const int*, const int*, const double*, int);
-template void launch_combine_env<float>(ttn_ctx*, const float*, long long, long long, float*,
+template void launch_combine_env<float>(ttn_ctx*, const float*, long long, int, int, float*,
                                         int, int, const int*, const int*, const float*, int);
 
 // ---- bulk copies (cp.async.bulk, the 1-D TMA path) completing on an mbarrier --------------------
@@ -770,15 +776,16 @@ __host__ __device__ __forceinline__ int level_env_floats(int K) {
   return TC ? 2 * NA * (K + 4) : K * NA;
 }
 
-// raw slice Er[a * K + b] (a < N) -> compute layout (padding columns zero); whole CTA
+// raw slice (Er[a * K + b], or Er[b * N + a] when et) -> compute layout (padding columns zero);
+// whole CTA
 template <int NA, bool TC>
-__device__ __forceinline__ void level_stage_env(const float* Er, float* Ec, int N, int K) {
+__device__ __forceinline__ void level_stage_env(const float* Er, float* Ec, int N, int K, bool et) {
   if constexpr (TC) {
     uint32_t* Eh = reinterpret_cast<uint32_t*>(Ec);
     uint32_t* El = Eh + NA * (K + 4);
     for (int i = threadIdx.x; i < NA * K; i += blockDim.x) {
       const int n = i / K, k = i - n * K;
-      const float x = n < N ? Er[n * K + k] : 0.f;
+      const float x = n < N ? Er[et ? k * N + n : n * K + k] : 0.f;
       const uint32_t hi = tf32_bits(x);
       Eh[n * (K + 4) + k] = hi;
       El[n * (K + 4) + k] = tf32_bits(x - __uint_as_float(hi));
@@ -786,7 +793,7 @@ __device__ __forceinline__ void level_stage_env(const float* Er, float* Ec, int 
   } else {
     for (int i = threadIdx.x; i < K * NA; i += blockDim.x) {
       const int b = i / NA, a = i - b * NA;
-      Ec[i] = a < N ? Er[a * K + b] : 0.f;
+      Ec[i] = a < N ? Er[et ? b * N + a : a * K + b] : 0.f;
     }
   }
 }
@@ -903,7 +910,7 @@ __device__ __forceinline__ void level_store(float* dst, int nrow, int N, const f
 // the one staged tile.
 template <int NA, bool TC>
 __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, int rows_cta,
-                                                        int sb_max, int vec_store) {
+                                                        int sb_max, int vec_store, int et) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ __align__(8) unsigned long long bar;
   const int lda = TC ? rows_cta + 8 : rows_cta;
@@ -938,7 +945,8 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
   }
   const bool ok = mbar_wait(&bar, 0, g.wait_flag);
   if (__syncthreads_or(!ok)) return;
-  for (int j = 0; j < ns; ++j) level_stage_env<NA, TC>(Er + j * nk4, Ec + j * esz, g.N, g.K);
+  for (int j = 0; j < ns; ++j)
+    level_stage_env<NA, TC>(Er + j * nk4, Ec + j * esz, g.N, g.K, et != 0);
   __syncthreads();
   if ((threadIdx.x >> 5) * 32 >= nrow) return;   // whole warps only (MMA needs all lanes)
   long long cidx = 0;
@@ -962,7 +970,7 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
 // is requested once segment j has been consumed) and accumulate in registers.
 template <int NA, bool TC>
 __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtiles, int rows_cta,
-                                                            int vec_store) {
+                                                            int vec_store, int et) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ __align__(8) unsigned long long bar[2];
   const int lda = TC ? rows_cta + 8 : rows_cta;
@@ -1010,7 +1018,7 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
     const float* As = dsm + st * stage;
     const float* Er = As + g.K * lda;
     float* Ec = const_cast<float*>(Er) + nk4;
-    level_stage_env<NA, TC>(Er, Ec, g.N, g.K);
+    level_stage_env<NA, TC>(Er, Ec, g.N, g.K, et != 0);
     __syncthreads();
     if (live) level_mac<NA, TC>(As, lda, Ec, g.K, acc);
     __syncthreads();
@@ -1027,6 +1035,83 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
   level_store<NA, TC>(static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
                           (long long)r0 * g.N,
                       nrow, g.N, acc, vec_store);
+}
+
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Segmented level stage, warp-specialised (float32 SIMT compute, slices stored [b][a] with
+// N = NA, i.e. already in the compute layout). Warps 0..nw-1 compute (32 rows each), warp nw
+// produces: its first lane requests segment j's A tile and slice into stage j % 2 once the
+// compute warps have released that stage (an "empty" mbarrier with one arrival per compute
+// warp), and the copies complete a "full" mbarrier the compute warps wait on. No CTA-wide
+// barrier inside the segment loop; every wait is bounded.
+template <int NA>
+__global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtiles, int rows_cta,
+                                                           int vec_store) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long full[2];
+  __shared__ __align__(8) unsigned long long empty[2];
+  const int nw = rows_cta >> 5;
+  const int stage = g.K * rows_cta + g.K * NA;
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const int s0 = g.st.seg_ptr[sub], nseg = g.st.seg_ptr[sub + 1] - s0;
+  const int r0 = rt * rows_cta;
+  const int nrow = min(rows_cta, g.M - r0);
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], nw);
+    mbar_init(&empty[1], nw);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == nw) {
+    if (lane == 0) {
+      const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+      const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+      for (int j = 0; j < nseg; ++j) {
+        const int st = j & 1;
+        if (j >= 2 && !mbar_wait(&empty[st], ((j >> 1) - 1) & 1, g.wait_flag)) break;
+        fence_proxy_async();
+        float* As = dsm + st * stage;
+        float* Es = As + g.K * rows_cta;
+        const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
+        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
+        for (int b = 0; b < g.K; ++b)
+          bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
+        bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
+      }
+    }
+    return;
+  }
+  const bool live = warp * 32 < nrow;   // warp-uniform
+  float acc[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+  for (int j = 0; j < nseg; ++j) {
+    const int st = j & 1;
+    if (!mbar_wait(&full[st], (j >> 1) & 1, g.wait_flag)) return;
+    const float* As = dsm + st * stage;
+    if (live) level_mac<NA, false>(As, rows_cta, As + g.K * rows_cta, g.K, acc);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  if (!live) return;
+  long long cidx = 0;
+  if (g.c_mode == MODE_PAIR) cidx = pair;
+  else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+  else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+  level_store<NA, false>(static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
+                             (long long)r0 * g.N,
+                         nrow, g.N, acc, vec_store);
 }
 
 namespace {
@@ -1067,8 +1152,9 @@ int level_group_cap(int M, int N, int K) {
 static bool level_tma_ok(const GemmDesc& g) {
   if (level_group_cap(g.M, g.N, g.K) <= 0) return false;
   if (g.st.n_grp <= 0 && level_tma_seg_smem(g.M, g.N, g.K, true) > kLevelTmaSmem) return false;
-  if (g.a_sm != 1 || g.a_sk % 4 != 0 || g.b_sk != 1 || g.b_sn != g.K || g.c_sm != g.N ||
-      g.c_sn != 1)
+  const bool e_ab = g.b_sk == 1 && g.b_sn == g.K;   // slices stored [a][b]
+  const bool e_ba = g.b_sn == 1 && g.b_sk == g.N;   // slices stored [b][a]
+  if (g.a_sm != 1 || g.a_sk % 4 != 0 || !(e_ab || e_ba) || g.c_sm != g.N || g.c_sn != 1)
     return false;
   if (g.A.pstride % 4 != 0 || g.B.pstride % 4 != 0) return false;
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
@@ -1112,10 +1198,30 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     LaunchScope ls(ctx, (tc ? nm_tc : nm)[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(T)));
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
+    const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
+    if (!tc && et && g.N == na) {
+      // slices already in the compute layout: warp-specialised copy/compute pipeline
+      const size_t smem_ws = sizeof(float) * 2 * ((size_t)g.K * rows_cta + (size_t)g.K * na);
+      auto go_ws = [&](auto kern) {
+        CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kLevelTmaSmem));
+        kern<<<(unsigned)grid, rows_cta + 32, smem_ws, ctx->stream>>>(gd, rt, rows_cta,
+                                                                        vec ? 1 : 0);
+      };
+      switch (na) {
+        case 8: go_ws(level_seg_ws_kernel<8>); break;
+        case 16: go_ws(level_seg_ws_kernel<16>); break;
+        case 24: go_ws(level_seg_ws_kernel<24>); break;
+        default: go_ws(level_seg_ws_kernel<32>); break;
+      }
+      CUDA_LAUNCH_CHECK();
+      return;
+    }
     auto go = [&](auto kern) {
       CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kLevelTmaSmem));
-      kern<<<(unsigned)grid, rows_cta, smem, ctx->stream>>>(gd, rt, rows_cta, vec ? 1 : 0);
+      kern<<<(unsigned)grid, rows_cta, smem, ctx->stream>>>(gd, rt, rows_cta, vec ? 1 : 0,
+                                                            et ? 1 : 0);
     };
     if (tc) {
       switch (na) {
@@ -1161,7 +1267,9 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     auto go = [&](auto kern) {
       CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kLevelTmaSmem));
-      kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0);
+      const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
+      kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0,
+                                                           et ? 1 : 0);
     };
     if (tc) {
       switch (na) {
