@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int r
   else if (o.A.mode == MODE_BRA) aidx = o.pair_bra[pair];
   const T* Tb = static_cast<const T*>(o.A.base) + aidx * o.A.pstride;
   const T* ops = static_cast<const T*>(o.ops);
-  const int r0 = rt * kThreads;
+  const int r0 = rt * (int)blockDim.x;   // row tile = blockDim.x rows (<= kThreads)
   const int r = r0 + threadIdx.x;
   T acc[D];
 #pragma unroll
@@ -453,9 +453,9 @@ __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int r
   __shared__ int spre[GCH];
   for (int gc = g0; gc < g1; gc += GCH) {
     const int ng = min(GCH, g1 - gc);
-    for (int i = threadIdx.x; i < ng * D * D; i += kThreads)
+    for (int i = threadIdx.x; i < ng * D * D; i += blockDim.x)
       sop[i] = ops[(long long)gc * D * D + i];
-    for (int i = threadIdx.x; i < ng; i += kThreads) spre[i] = o.grp_prefix[gc + i];
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) spre[i] = o.grp_prefix[gc + i];
     __syncthreads();
     if (r < o.rows) {
       int g = 0;
@@ -495,13 +495,14 @@ __global__ void __launch_bounds__(kThreads) op_stage_kernel(OpStageDesc o, int r
   __syncthreads();
   T* Zb = static_cast<T*>(o.Z) + (long long)pair * o.z_pstride +
           (long long)slot * o.rows * D + (long long)r0 * D;
-  const int nrow = min(kThreads, o.rows - r0);
-  for (int i = threadIdx.x; i < nrow * D; i += kThreads)
+  const int nrow = min((int)blockDim.x, o.rows - r0);
+  for (int i = threadIdx.x; i < nrow * D; i += blockDim.x)
     Zb[i] = sout[(i / D) * (D + 1) + (i % D)];
 }
 
 template <class T, int D>
-static void op_stage_dispatch(ttn_ctx* ctx, const OpStageDesc& o, int rtiles, long long grid) {
+static void op_stage_dispatch(ttn_ctx* ctx, const OpStageDesc& o, int rtiles, long long grid,
+                              int tile) {
   constexpr int GCH = op_stage_chunk<T, D>();
   const size_t shmem = sizeof(T) * ((size_t)GCH * D * D + (size_t)kThreads * (D + 1));
   static int set_for_device[64] = {0};
@@ -510,7 +511,7 @@ static void op_stage_dispatch(ttn_ctx* ctx, const OpStageDesc& o, int rtiles, lo
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmem));
     set_for_device[ctx->device] = 1;
   }
-  op_stage_kernel<T, D><<<grid, kThreads, shmem, ctx->stream>>>(o, rtiles);
+  op_stage_kernel<T, D><<<grid, tile, shmem, ctx->stream>>>(o, rtiles);
 }
 
 template <class T>
@@ -526,7 +527,10 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
   TTN_REQUIRE((long long)o.n_pairs * o.z_pstride <= o.z_len &&
                   (long long)o.n_slots * o.rows * o.d <= o.z_pstride,
               "op stage bounds: Z");
-  const int rtiles = (o.rows + kThreads - 1) / kThreads;
+  // row tiles split the rows evenly, in whole warps (576 rows: 3 x 192; 9 rows: 1 x 32)
+  const int nt = (o.rows + kThreads - 1) / kThreads;
+  const int tile = ((o.rows + nt - 1) / nt + 31) / 32 * 32;
+  const int rtiles = (o.rows + tile - 1) / tile;
   const long long grid = (long long)rtiles * o.n_slots * o.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "op stage grid too large");
   const double flops = 2.0 * o.d * o.d * (double)o.rows * o.n_groups * o.n_pairs;
@@ -534,7 +538,7 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
                        ((double)o.n_unique_prefix * o.tsize + (double)o.n_slots * o.rows * o.d);
   LaunchScope ls(ctx, sizeof(T) == 8 ? "op_stage_f64" : "op_stage_f32", flops, bytes);
   switch (o.d) {
-#define TTN_OPD(k) case k: op_stage_dispatch<T, k>(ctx, o, rtiles, grid); break;
+#define TTN_OPD(k) case k: op_stage_dispatch<T, k>(ctx, o, rtiles, grid, tile); break;
     TTN_OPD(1) TTN_OPD(2) TTN_OPD(3) TTN_OPD(4) TTN_OPD(5) TTN_OPD(6) TTN_OPD(7) TTN_OPD(8)
     TTN_OPD(9) TTN_OPD(10) TTN_OPD(11) TTN_OPD(12) TTN_OPD(13) TTN_OPD(14) TTN_OPD(15)
     TTN_OPD(16) TTN_OPD(17) TTN_OPD(18) TTN_OPD(19) TTN_OPD(20) TTN_OPD(21) TTN_OPD(22)
