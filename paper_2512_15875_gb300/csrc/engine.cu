@@ -228,6 +228,12 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
         const size_t e = std::min(kv.second.size(), i + (size_t)cap);
         s.grp_sub.insert(s.grp_sub.end(), kv.second.begin() + i, kv.second.begin() + e);
         s.grp_ptr.push_back((int)s.grp_sub.size());
+        s.grp_a.push_back(kv.first);
+        for (size_t k = i; k < e; ++k) {
+          const int j = kv.second[k];
+          s.grp_b.push_back(s.seg_b[s.seg_ptr[j]]);
+          s.grp_c.push_back(s.sub_c[j]);
+        }
       }
   }
   if (out_kind == OUT_ENV) {
@@ -246,7 +252,8 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
   size_t bytes = 0;
   for (auto& s : hs) {
     bytes += (s.sub_c.size() + s.seg_a.size() + s.seg_b.size()) * sizeof(long long);
-    bytes += (s.seg_ptr.size() + s.grp_ptr.size() + s.grp_sub.size()) * sizeof(int) + 7 * 16;
+    bytes += (s.seg_ptr.size() + s.grp_ptr.size() + s.grp_sub.size()) * sizeof(int) +
+             (s.grp_a.size() + s.grp_b.size() + s.grp_c.size()) * sizeof(long long) + 10 * 16;
   }
   std::vector<char> host(bytes + 64, 0);
   DevTables t;
@@ -270,6 +277,9 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
     ds.n_grp = (int)s.grp_ptr.size() - 1;
     ds.grp_ptr = (const int*)put(s.grp_ptr.data(), s.grp_ptr.size() * sizeof(int));
     ds.grp_sub = (const int*)put(s.grp_sub.data(), s.grp_sub.size() * sizeof(int));
+    ds.grp_a = (const long long*)put(s.grp_a.data(), s.grp_a.size() * sizeof(long long));
+    ds.grp_b = (const long long*)put(s.grp_b.data(), s.grp_b.size() * sizeof(long long));
+    ds.grp_c = (const long long*)put(s.grp_c.data(), s.grp_c.size() * sizeof(long long));
     t.stages.push_back(ds);
   }
   t.host = hs;

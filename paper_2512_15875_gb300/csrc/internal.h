@@ -182,11 +182,15 @@ struct StageDev {
   int n_grp = 0;                    // 0: no A groups (some item has several segments)
   const int* grp_ptr = nullptr;     // CSR over grp_sub, n_grp + 1 entries
   const int* grp_sub = nullptr;
+  const long long* grp_a = nullptr;   // per group: the shared A offset
+  const long long* grp_b = nullptr;   // per member (aligned with grp_sub): its B offset
+  const long long* grp_c = nullptr;   // per member: its C offset
 };
 struct StageHost {
   std::vector<long long> sub_c, seg_a, seg_b;
   std::vector<int> seg_ptr{0};
   std::vector<int> grp_ptr{0}, grp_sub;
+  std::vector<long long> grp_a, grp_b, grp_c;
 };
 struct DevTables {
   DevBuf buf;   // all item tables of one (plan, dims) in one allocation

@@ -939,13 +939,12 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const float* Ab = Abase + g.st.seg_a[g.st.seg_ptr[g.st.grp_sub[gs]]] + r0;
+    const float* Ab = Abase + g.st.grp_a[q] + r0;
     mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
     for (int b = 0; b < g.K; ++b)
       bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
     for (int j = 0; j < ns; ++j)
-      bulk_copy_g2s(Er + j * nk4, Bbase + g.st.seg_b[g.st.seg_ptr[g.st.grp_sub[gs + j]]],
-                    g.N * g.K * 4u, &bar);
+      bulk_copy_g2s(Er + j * nk4, Bbase + g.st.grp_b[gs + j], g.N * g.K * 4u, &bar);
   }
   const bool ok = mbar_wait(&bar, 0, g.wait_flag);
   if (__syncthreads_or(!ok)) return;
@@ -963,8 +962,8 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
 #pragma unroll
     for (int i = 0; i < NA; ++i) acc[i] = 0.f;
     level_mac<NA, TC>(As, lda, Ec + j * esz, g.K, acc);
-    level_store<NA, TC>(Cpair + g.st.sub_c[g.st.grp_sub[gs + j]] + (long long)r0 * g.N, nrow,
-                        g.N, acc, vec_store);
+    level_store<NA, TC>(Cpair + g.st.grp_c[gs + j] + (long long)r0 * g.N, nrow, g.N, acc,
+                        vec_store);
   }
 }
 
