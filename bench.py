@@ -216,6 +216,16 @@ def measured_traffic(name, rec):
             "profiles/dram_traffic.md")
 
 
+def kernel_table(prof, steps, top=12):
+    """The kernels with the largest event time in the timed region: ms per step, launches per
+    step, share of the summed kernel time."""
+    ks = {k: v for k, v in prof.items() if not k.startswith("phase:")}
+    tot = max(sum(v["ms"] for v in ks.values()), 1e-9)
+    rows = sorted(ks.items(), key=lambda kv: -kv[1]["ms"])[:top]
+    return {k: {"ms": round(v["ms"] / steps, 3), "launches": v["launches"] / steps,
+                "share": round(v["ms"] / tot, 4)} for k, v in rows}
+
+
 def aggregate_replicas(t, n_conv, dist, device="cpu"):
     """Whole-job numbers of independent replicas: the slowest rank's time and the states
     converged on all ranks (no collective touches the data path; this is bookkeeping)."""
@@ -503,6 +513,7 @@ def main():
         "gpu_launches": out["launches"],
         "phases_ms_per_step": {k[6:]: v["ms"] / args.steps for k, v in out["prof"].items()
                                if k.startswith("phase:")},
+        "kernels_ms_per_step": kernel_table(out["prof"], args.steps),
     }
     if "gram" in out:
         g = out["gram"]
