@@ -27,6 +27,20 @@ long long key_of(int node, int open) { return (long long)node * 64 + (open + 1);
 
 }  // namespace
 
+void StageHost::finalize() {
+  n_ua = (long long)std::set<long long>(seg_a.begin(), seg_a.end()).size();
+  n_ub = (long long)std::set<long long>(seg_b.begin(), seg_b.end()).size();
+  n_seg = (long long)seg_a.size();
+  single = true;
+  for (size_t j = 0; j + 1 < seg_ptr.size(); ++j) single = single && seg_ptr[j + 1] - seg_ptr[j] == 1;
+  a4 = b4 = c2 = true;
+  for (long long a : seg_a) a4 = a4 && a % 4 == 0;
+  for (long long b : seg_b) b4 = b4 && b % 4 == 0;
+  for (long long c : sub_c) c2 = c2 && c % 2 == 0;
+  grp_max = 0;
+  for (size_t q = 0; q + 1 < grp_ptr.size(); ++q) grp_max = std::max(grp_max, grp_ptr[q + 1] - grp_ptr[q]);
+}
+
 NodePlan& get_plan(ttn_ttno* H, int t, int open) {
   const long long key = key_of(t, open);
   auto it = H->plans.find(key);
@@ -248,6 +262,7 @@ DevTables& get_tables(ttn_ttno* H, const NodePlan& p, const std::vector<int>& Da
     }
     hs.push_back(std::move(s));
   }
+  for (auto& s : hs) s.finalize();
   // pack into one device buffer
   size_t bytes = 0;
   for (auto& s : hs) {

@@ -191,6 +191,14 @@ struct StageHost {
   std::vector<int> seg_ptr{0};
   std::vector<int> grp_ptr{0}, grp_sub;
   std::vector<long long> grp_a, grp_b, grp_c;
+  // facts the launchers need on every launch, computed once when the tables are built
+  long long n_ua = -1, n_ub = -1;   // distinct A / B offsets (-1: not computed)
+  long long n_seg = 0;              // segments over all items
+  bool single = true;               // every item has exactly one segment
+  bool a4 = true, b4 = true;        // every A / B offset a multiple of 4 elements
+  bool c2 = true;                   // every C offset even
+  int grp_max = 0;                  // largest A group
+  void finalize();
 };
 struct DevTables {
   DevBuf buf;   // all item tables of one (plan, dims) in one allocation

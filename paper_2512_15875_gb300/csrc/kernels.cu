@@ -2,6 +2,7 @@
 // segment sums (the workhorse of every node contraction), tensor permutes, per-pair dots.
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <set>
 
 #include "internal.h"
@@ -211,19 +212,32 @@ int grid_for(long long n) {
 
 }  // namespace
 
+// Raises a kernel's dynamic shared-memory limit once per (kernel, device).
+static void smem_attr(const void* fn, int bytes, int device) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({fn, device})) return;
+  CUDA_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done.insert({fn, device});
+}
+
 // Algorithmic bytes of a strided batched launch: every distinct A and B slice read once per
 // distinct base (pair / bra / ket index), every output item written once.
 static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
-  std::set<long long> ua(g.hst->seg_a.begin(), g.hst->seg_a.end());
-  std::set<long long> ub(g.hst->seg_b.begin(), g.hst->seg_b.end());
+  double n_ua = (double)g.hst->n_ua, n_ub = (double)g.hst->n_ub;
+  if (g.hst->n_ua < 0 || g.hst->n_ub < 0) {
+    n_ua = (double)std::set<long long>(g.hst->seg_a.begin(), g.hst->seg_a.end()).size();
+    n_ub = (double)std::set<long long>(g.hst->seg_b.begin(), g.hst->seg_b.end()).size();
+  }
   auto bases = [&](int mode) -> double {
     if (mode == MODE_PAIR) return g.n_pairs;
     if (mode == MODE_BRA) return std::min(g.n_pairs, g.max_bra + 1);
     if (mode == MODE_KET) return std::min(g.n_pairs, g.max_ket + 1);
     return 1.0;
   };
-  const double a = bases(g.A.mode) * (double)ua.size() * g.M * g.K;
-  const double b = bases(g.B.mode) * (double)ub.size() * g.N * g.K;
+  const double a = bases(g.A.mode) * n_ua * g.M * g.K;
+  const double b = bases(g.B.mode) * n_ub * g.N * g.K;
   const double c = (double)g.n_pairs * g.st.n_sub * g.M * g.N;
   return (double)elem * (a + b + c);
 }
@@ -1162,11 +1176,7 @@ static bool level_tma_ok(const GemmDesc& g) {
   if (g.A.pstride % 4 != 0 || g.B.pstride % 4 != 0) return false;
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
     return false;
-  for (long long a : g.hst->seg_a)
-    if (a % 4) return false;
-  for (long long b : g.hst->seg_b)
-    if (b % 4) return false;
-  return true;
+  return g.hst->a4 && g.hst->b4;
 }
 
 template <class T>
@@ -1188,12 +1198,10 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     const size_t smem = level_tma_seg_smem(g.M, g.N, g.K, tc);
     bool vec = g.N == na && g.c_pstride % 2 == 0 &&
                reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
-    for (long long c0 : g.hst->sub_c) vec = vec && c0 % 2 == 0;
+    vec = vec && g.hst->c2;
     const long long grid = (long long)rt * g.st.n_sub * g.n_pairs;
     TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
-    long long nseg = 0;
-    for (int q = 0; q < g.st.n_sub; ++q) nseg += g.hst->seg_ptr[q + 1] - g.hst->seg_ptr[q];
-    const double flops = 2.0 * g.M * g.N * (double)g.K * nseg * g.n_pairs;
+    const double flops = 2.0 * g.M * g.N * (double)g.K * g.hst->n_seg * g.n_pairs;
     static const char* nm[] = {"level_tma_seg_f32_8", "level_tma_seg_f32_16",
                                "level_tma_seg_f32_24", "level_tma_seg_f32_32"};
     static const char* nm_tc[] = {"level_tma_seg_tf32x3_8", "level_tma_seg_tf32x3_16",
@@ -1206,8 +1214,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
       // slices already in the compute layout: warp-specialised copy/compute pipeline
       const size_t smem_ws = sizeof(float) * 2 * ((size_t)g.K * rows_cta + (size_t)g.K * na);
       auto go_ws = [&](auto kern) {
-        CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kLevelTmaSmem));
+        smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
         kern<<<(unsigned)grid, rows_cta + 32, smem_ws, ctx->stream>>>(gd, rt, rows_cta,
                                                                         vec ? 1 : 0);
       };
@@ -1221,8 +1228,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
       return;
     }
     auto go = [&](auto kern) {
-      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kLevelTmaSmem));
+      smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
       kern<<<(unsigned)grid, rows_cta, smem, ctx->stream>>>(gd, rt, rows_cta, vec ? 1 : 0,
                                                             et ? 1 : 0);
     };
@@ -1248,14 +1254,12 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     const int na = level_tma_na(g.N);
     const int rows_cta = level_tma_rows(g.M);
     const int rt = (g.M + rows_cta - 1) / rows_cta;
-    int sb_max = 0;
-    for (int q = 0; q < g.st.n_grp; ++q)
-      sb_max = std::max(sb_max, g.hst->grp_ptr[q + 1] - g.hst->grp_ptr[q]);
+    const int sb_max = g.hst->grp_max;
     const size_t smem = level_tma_smem(g.M, g.N, g.K, sb_max, tc);
     TTN_REQUIRE(smem <= kLevelTmaSmem, "level kernel: A group larger than its cap");
     bool vec = g.N == na && g.c_pstride % 2 == 0 &&
                reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
-    for (long long c0 : g.hst->sub_c) vec = vec && c0 % 2 == 0;
+    vec = vec && g.hst->c2;
     const long long grid = (long long)rt * g.st.n_grp * g.n_pairs;
     TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
     const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
@@ -1268,8 +1272,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     gd.wait_flag = ctx->d_wait;
     const int threads = rows_cta;   // 32 rows per warp
     auto go = [&](auto kern) {
-      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kLevelTmaSmem));
+      smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
       const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
       kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0,
                                                            et ? 1 : 0);
@@ -1534,10 +1537,7 @@ static bool closure_tma_ok(const GemmDesc& g) {
     return false;
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
     return false;
-  for (long long a : g.hst->seg_a)
-    if (a % 4) return false;
-  for (long long b : g.hst->seg_b)
-    if (b % 4) return false;
+  if (!g.hst->a4 || !g.hst->b4) return false;
   return closure_tma_smem(g.K, pad) <= kClosureTmaSmem;
 }
 
@@ -1625,9 +1625,7 @@ constexpr size_t kClosureSmallSmem = 96 * 1024;
 
 bool closure_shape_ok(const GemmDesc& g) {
   if (g.a_sk != 1 || g.b_sk != 1 || g.M > 32 || g.N > 32) return false;
-  for (int s = 0; s < g.st.n_sub; ++s)
-    if (g.hst->seg_ptr[s + 1] - g.hst->seg_ptr[s] != 1) return false;
-  return true;
+  return g.hst->single;
 }
 
 template <class T>
@@ -1646,8 +1644,7 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
     const size_t smem = closure_small_smem(g.K, pad_small, sizeof(T));
     LaunchScope ls(ctx, "closure_small_f32", flops, bytes);
     auto go = [&](auto kern) {
-      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kClosureSmallSmem));
+      smem_attr((const void*)kern, (int)kClosureSmallSmem, ctx->device);
       kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(g, ldk);
     };
     if (pad_small == 12) go(closure_small_kernel<float, 3, 3, 12, 12>);
@@ -1665,8 +1662,7 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
     auto go = [&](auto kern) {
-      CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kClosureTmaSmem));
+      smem_attr((const void*)kern, (int)kClosureTmaSmem, ctx->device);
       kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(gd, kc_max, nstage);
     };
     if (pad == 12) go(closure_tma_kernel<3, 3, 12, 12>);
