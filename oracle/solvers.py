@@ -28,12 +28,19 @@ from .network import (environments, expectation, identity_ttno, legs, node_contr
 # ----------------------------------------------------------------------------------------------
 
 
-def minres(matvec, b, x0=None, tol=1e-5, maxiter=10):
+def minres(matvec, b, x0=None, tol=1e-5, maxiter=10, eps=np.finfo(np.float64).eps):
     """Minimum-residual Krylov solve of A x = b for symmetric (possibly indefinite) A.
 
     Lanczos three-term recurrence for T_k, QR of T_k by Givens rotations, and the update of x by
     the direction vectors w_k. Returns (x, residual norms |phibar_k| starting with the initial
     residual), which is non-increasing by construction.
+
+    Stopping (Paige & Saunders 1975): |phibar_k| <= tol * |b|, a Lanczos breakdown
+    (beta_{k+1} = 0), maxiter steps, or the residual at the rounding level of the iterate,
+    |phibar_k| <= eps * (|T_k|_F * |x_k| + |b|) with |T_k|_F^2 = sum_j (alpha_j^2 + beta_j^2 +
+    beta_{j+1}^2): past that point the computed residual no longer describes x_k and further
+    steps only add rounding. Inverse iteration with a converged Rayleigh-quotient shift (Alg. 3)
+    meets it: (A - s) is then singular to working precision and x_k grows along the eigenvector.
     """
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - matvec(x) if x0 is not None else b.copy()
@@ -49,12 +56,14 @@ def minres(matvec, b, x0=None, tol=1e-5, maxiter=10):
     w_prev = np.zeros_like(b)
     w_prev2 = np.zeros_like(b)
     phibar = beta1
+    tnorm2 = 0.0
     for _ in range(maxiter):
         p = matvec(v)
         alpha = float(np.vdot(v, p))
         p = p - alpha * v - beta * v_prev
         beta_next = float(np.linalg.norm(p))
-        eps = s2 * beta
+        tnorm2 += alpha * alpha + beta * beta + beta_next * beta_next
+        epsk = s2 * beta
         dtil = c2 * beta
         delta = c1 * dtil + s1 * alpha
         gtil = -s1 * dtil + c1 * alpha
@@ -64,12 +73,14 @@ def minres(matvec, b, x0=None, tol=1e-5, maxiter=10):
         c, s = gtil / gamma, beta_next / gamma
         tau = c * phibar
         phibar = -s * phibar
-        w = (v - delta * w_prev - eps * w_prev2) / gamma
+        w = (v - delta * w_prev - epsk * w_prev2) / gamma
         x = x + tau * w
         hist.append(abs(phibar))
         c2, s2, c1, s1 = c1, s1, c, s
         w_prev2, w_prev = w_prev, w
         if beta_next == 0.0 or abs(phibar) <= tol * bnorm:
+            break
+        if abs(phibar) <= eps * (np.sqrt(tnorm2) * float(np.linalg.norm(x)) + bnorm):
             break
         v_prev, v = v, p / beta_next
         beta = beta_next

@@ -247,7 +247,7 @@ __global__ void seg_sum_kernel(const T* __restrict__ Y, const int* __restrict__ 
 // ---- MINRES (batched over states; scalars in float64) ----------------------------------------
 enum { MR_BETA1, MR_BNORM, MR_BETA, MR_C1, MR_S1, MR_C2, MR_S2, MR_PHIBAR, MR_ACTIVE, MR_ALPHA,
        MR_BNEXT2, MR_DELTA, MR_EPS, MR_GAMMA, MR_TAU, MR_BNEXT, MR_UPD, MR_CONT, MR_ITS,
-       MR_HITCAP, MR_NFIELDS };
+       MR_HITCAP, MR_TNORM2, MR_NFIELDS };
 
 __global__ void mr_init_scalars(double* sc, const double* bb, const double* rr, int n) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,6 +265,7 @@ __global__ void mr_init_scalars(double* sc, const double* bb, const double* rr, 
   f[MR_ACTIVE] = (beta1 > 0.0 && bnorm > 0.0) ? 1.0 : 0.0;
   f[MR_ITS] = 0.0;
   f[MR_HITCAP] = 0.0;
+  f[MR_TNORM2] = 0.0;
 }
 
 // r = b - Ax (in p), v = r / beta1, vp = 0, w1 = w2 = 0
@@ -315,6 +316,7 @@ __global__ void mr_step_scalars(double* sc, const double* alpha, const double* b
   if (f[MR_ACTIVE] == 0.0) return;
   const double a = alpha[s], beta = f[MR_BETA];
   const double bnext = sqrt(fmax(bnext2[s], 0.0));
+  f[MR_TNORM2] += a * a + beta * beta + bnext * bnext;
   const double eps = f[MR_S2] * beta;
   const double dtil = f[MR_C2] * beta;
   const double delta = f[MR_C1] * dtil + f[MR_S1] * a;
@@ -343,6 +345,23 @@ __global__ void mr_step_scalars(double* sc, const double* alpha, const double* b
   f[MR_ACTIVE] = conv ? 0.0 : 1.0;
   if (!conv && f[MR_ITS] >= maxiter) f[MR_HITCAP] = 1.0;
   f[MR_BETA] = bnext;
+}
+
+// Paige-Saunders stop on the rounding level of the iterate: a state that is still running stops
+// once |phibar_k| <= eps_T * (|T_k|_F |x_k| + |b|) (|x_k|^2 in xx, eps_T the machine epsilon
+// of the vector type). Beyond it the recurrence residual no longer describes x_k; this is what a
+// Rayleigh-quotient shift that has converged to working precision runs into (Alg. 3).
+__global__ void mr_floor_check(double* sc, const double* xx, int n, double eps) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double* f = sc + (long long)s * MR_NFIELDS;
+  if (f[MR_UPD] == 0.0 || f[MR_CONT] == 0.0) return;
+  const double floor_r = eps * (sqrt(f[MR_TNORM2]) * sqrt(fmax(xx[s], 0.0)) + f[MR_BNORM]);
+  if (fabs(f[MR_PHIBAR]) <= floor_r) {
+    f[MR_CONT] = 0.0;
+    f[MR_ACTIVE] = 0.0;
+    f[MR_HITCAP] = 0.0;
+  }
 }
 
 template <class T>
@@ -936,7 +955,8 @@ static bool minres_batched(ttn_ctx* ctx, ttn_ttno* H, EnvCache<T>& env, int t,
   T* w1 = bufs[3].as<T>();
   T* w2 = bufs[4].as<T>();
   DevBuf sc((size_t)n * MR_NFIELDS * sizeof(double), st), d1(n * sizeof(double), st),
-      d2(n * sizeof(double), st);
+      d2(n * sizeof(double), st), d3(n * sizeof(double), st);
+  const double eps_t = sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
   std::vector<const T*> envs = env.node_envs(t);
   std::vector<int> da(shape->tree.nlegs(t));
   for (int m = 0; m < (int)da.size(); ++m) da[m] = shape->bdim(t, m);
@@ -989,6 +1009,12 @@ static bool minres_batched(ttn_ctx* ctx, ttn_ttno* H, EnvCache<T>& env, int t,
       LaunchScope ls(ctx, "minres_vec", 8.0 * total, 8.0 * sizeof(T) * total);
       mr_step_vectors<T><<<grid_of(total), kT, 0, st>>>(sc.as<double>(), x, v, vp, w1, w2, p,
                                                         sz, n);
+      CUDA_LAUNCH_CHECK();
+    }
+    launch_dot<T>(ctx, x, x, sz, n, d3.as<double>());
+    {
+      LaunchScope ls(ctx, "minres_scalar", 0.0, 0.0);
+      mr_floor_check<<<(n + 127) / 128, 128, 0, st>>>(sc.as<double>(), d3.as<double>(), n, eps_t);
       CUDA_LAUNCH_CHECK();
     }
   };

@@ -290,3 +290,83 @@ def test_lobpcg_reaches_the_uncoupled_closed_form():
     lam, X, hist = S.lobpcg(tree, T, X0, 4, shift=lambda l: l[0] - 50.0)
     ref = closed.uncoupled_levels(omega, [4, 4, 4], 3)
     assert np.abs(lam - ref).max() <= 1e-10 * ref[0]
+
+
+def test_minres_stops_at_the_rounding_floor_of_a_converged_shift():
+    # (A - s) with s the Rayleigh quotient of a nearly exact eigenvector is singular to working
+    # precision: MINRES stops on Paige & Saunders' rounding-level test well before its cap and
+    # returns the eigenvector direction to rounding; without the test (eps = 0) the iteration
+    # runs to the cap and rounding leaks into the direction
+    rng = np.random.default_rng(4)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (Q * (3000.0 + np.concatenate([[0.0], np.linspace(50, 5000, n - 1)]))) @ Q.T
+    v1 = Q[:, 0]
+    worst_without = 0.0
+    for noise in (1e-9, 1e-11, 1e-13):
+        x = v1 + noise * rng.standard_normal(n)
+        x /= np.linalg.norm(x)
+        s = x @ A @ x
+        for eps in (np.finfo(np.float64).eps, 0.0):
+            y, h = S.minres(lambda v: A @ v - s * v, x, x0=x, tol=1e-14, maxiter=300, eps=eps)
+            y /= np.linalg.norm(y)
+            err = min(np.abs(y - v1).max(), np.abs(y + v1).max())
+            if eps > 0:
+                assert len(h) < 301 and err <= 1e-13
+            else:
+                assert len(h) == 301
+                worst_without = max(worst_without, err)
+    assert worst_without > 1e-11
+
+
+# --- block inverse iteration (Alg. 3) and its clustering rule (Sec. III.B) --------------------
+
+@pytest.mark.parametrize("lam,gap,blocks", [
+    ([0.0, 5.0, 10.0], 5.0, [[0], [1], [2]]),            # a gap equal to the threshold splits
+    ([0.0, 4.999, 9.998], 5.0, [[0, 1, 2]]),             # single linkage chains 0 - 4.999 - 9.998
+    ([10.0, 0.0, 3.0, 20.0], 5.0, [[1, 2], [0], [3]]),   # unsorted input, blocks in value order
+    ([1.0, 1.0, 1.0], 0.5, [[0, 1, 2]]),                 # ties join
+    ([1.0, 1.0, 1.0], 0.0, [[0], [1], [2]]),             # gap 0: one state per block
+    ([0.0, 1.0, 2.0, 3.0], 10.0, [[0, 1, 2, 3]]),        # one block
+    ([7.0, 3.0, 5.0], 1.0, [[1], [2], [0]]),             # all singletons, value order
+])
+def test_clusters_by_gap_table(lam, gap, blocks):
+    assert S.clusters_by_gap(np.array(lam), gap) == blocks
+
+
+def test_inverse_iteration_is_dense_inverse_iteration_at_full_bond():
+    # at full bond (c1, D = 36) one ALS step solves (H - s) y = x exactly, so Alg. 3 with one
+    # state is x <- (H - s I)^-1 x / |.| with s the Rayleigh quotient of x, step by step
+    w = I.make_workload("c1", D=36)
+    H = N.dense_hamiltonian(w.ham)
+    T = N.build_ttno(w.tree, w.ham)
+    blk = w.block(noise=1e-2)
+    for j in (0, 3):
+        xs = S.normalize(w.tree, [t[j] for t in blk])
+        v = N.ttns_to_dense(w.tree, xs)
+        for _ in range(4):
+            s = v @ H @ v
+            v = np.linalg.solve(H - s * np.eye(len(H)), v)
+            v /= np.linalg.norm(v)
+            _, X, hist = S.inverse_iteration(w.tree, T, [xs], 1, lambda l: [[0]], als_sweeps=2,
+                                             minres_max=400, minres_tol=1e-14)
+            xs = X[0]
+            xd = N.ttns_to_dense(w.tree, xs)
+            assert np.abs(np.sign(xd @ v) * xd - v).max() <= 1e-12
+            assert abs(hist[-1][0] - v @ H @ v) <= 1e-13 * abs(v @ H @ v)
+
+
+@pytest.mark.parametrize("gap", [0.0, 300.0])
+def test_inverse_iteration_reaches_the_lowest_dense_eigenvalues(gap):
+    # five product-like states at full bond: after six iterations every Rayleigh quotient is one
+    # of the five lowest eigenvalues of the dense Hamiltonian to 1e-10 relative, each reached once
+    w = I.make_workload("c1", D=36)
+    ev = np.linalg.eigvalsh(N.dense_hamiltonian(w.ham))
+    T = N.build_ttno(w.tree, w.ham)
+    blk = w.block(noise=1e-2)
+    X0 = [[t[j] for t in blk] for j in range(5)]
+    clusters = (lambda l: [[j] for j in range(len(l))]) if gap <= 0 else \
+        (lambda l: S.clusters_by_gap(l, gap))
+    lam, _, _ = S.inverse_iteration(w.tree, T, X0, 6, clusters, als_sweeps=2, minres_max=300,
+                                    minres_tol=1e-12)
+    assert np.abs(np.sort(lam) - ev[:5]).max() <= 1e-10 * ev[0]
