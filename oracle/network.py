@@ -314,8 +314,8 @@ def node_contract(tree, ttno, t, ket, envs, bra=None, open_leg=None):
     else:
         out = a + [p]
     r = np.einsum(*args, out, optimize=_PATH)
-    if bra is None:
-        r = r.reshape(ket.shape)
+    if bra is None and tree.phys_dim[t] == 0:
+        r = r[..., 0]            # auxiliary node: drop the size-one physical axis
     return r
 
 

@@ -36,7 +36,7 @@ __all__ = [
     "ho_matrices", "mps_tree", "fork_tree", "leaf_only_binary_tree", "all_physical_binary_tree",
     "cap_bonds", "uniform_bonds", "coupled_oscillators", "quartic_force_field",
     "uniform_coupled_model", "lowest_harmonic_configurations", "initial_block",
-    "make_workload", "WORKLOADS",
+    "make_workload", "WORKLOADS", "src_sketch",
 ]
 
 
@@ -379,6 +379,15 @@ def random_block(tree: Tree, bonds, n, seed, scale=1.0):
     """Dense N(0, scale^2) node tensors (for contraction tests)."""
     rng = np.random.default_rng(seed)
     return [scale * rng.standard_normal((n,) + node_shape(tree, bonds, i))
+            for i in range(tree.n_nodes)]
+
+
+def src_sketch(tree: Tree, chi: int, seed: int):
+    """The random matrices of the Khatri-Rao sketch of SRC (Sec. II.C.1): Omega^(i) of size
+    d_i x chi with N(0, 1) entries for every node with a physical leg, None for auxiliary
+    nodes."""
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((int(tree.phys_dim[i]), chi)) if tree.phys_dim[i] > 0 else None
             for i in range(tree.n_nodes)]
 
 
