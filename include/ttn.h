@@ -72,6 +72,11 @@ void ttn_destroy(ttn_ctx* ctx);
 const char* ttn_last_error(const ttn_ctx* ctx);
 /* Block the host until all work issued on the context's stream has finished. */
 ttn_status ttn_synchronize(ttn_ctx* ctx);
+/* Device time (CUDA events on the context's stream) from the start of the last ttn_lobpcg or
+ * ttn_inverse_iteration call on this context to the end of each of its iterations: ms[0] after
+ * the initial Rayleigh quotients, ms[i] after iteration i. Writes at most max_n values and
+ * returns how many the call recorded (0 if none, -1 on a CUDA error). */
+int ttn_iteration_times(ttn_ctx* ctx, double* ms, int max_n);
 /* Number of kernels this context has launched so far (for launch accounting). */
 long long ttn_launch_count(const ttn_ctx* ctx);
 /* Algorithmic flops of every contraction GEMM launched so far: 2*M*N*K per item and segment
@@ -85,6 +90,20 @@ ttn_status ttn_profile_enable(ttn_ctx* ctx, int on);
  * max_kernels entries; *n_kernels receives the number of distinct kernels (may exceed it). */
 ttn_status ttn_profile_get(ttn_ctx* ctx, int max_kernels, char* names, long long* launches,
                            double* ms, double* flops, double* bytes, int* n_kernels);
+
+/* ---- failure-path checks (no counterpart in the paper) ------------------------------------ */
+
+/* Runs one device block whose barrier wait can never complete (it announces a transfer that no
+ * copy delivers; nothing is in flight) with a wait budget of budget_ms (0.001 .. 1000 ms) and
+ * returns what every entry point returns after such a wait gives up: TTN_ETIMEOUT, with a
+ * message. The context stays usable afterwards. This exercises, without any GPU fault, the
+ * bounded waits that the bulk-copy kernels use (2 s budget); after a real TTN_ETIMEOUT from
+ * those kernels, copies may still have been in flight, and the context must be destroyed. */
+ttn_status ttn_selftest_bounded_wait(ttn_ctx* ctx, double budget_ms);
+/* Process-wide allocation-failure injection: after `after` further device allocations of the
+ * library succeed, the next one fails as an out-of-memory allocation would (the call that made
+ * it returns TTN_ENOMEM) and injection switches itself off. after < 0 switches it off. */
+void ttn_fault_inject_alloc(long long after);
 
 /* ---- tree (Sec. II.A.2, Eq. ttns; Appendix B trees) -------------------------------------- */
 
@@ -193,6 +212,21 @@ ttn_status ttn_gram(ttn_ctx* ctx, const ttn_ttno* H, const ttn_block* bra, const
 ttn_status ttn_apply_block(ttn_ctx* ctx, const ttn_ttno* H, const ttn_block* in,
                            ttn_block** out, ttn_precision prec);
 
+/* ---- successive randomized compression (Sec. II.C.1, Figs. random tensor and src) ------- */
+
+/* *out ~ H |x> for every state of x, by SRC with sketch dimension chi (1 .. 64). The sketch is
+ * the Khatri-Rao product of per-node random matrices Omega^(i) (d_i x chi), passed in `omega`:
+ * for every node with a physical leg, in node order, its d_i x chi matrix row-major (auxiliary
+ * nodes have none); chi * sum_i d_i doubles, owned by the caller. Leaves to root, each node's
+ * local sketch (the parent edge's sketched environment, the children's residual environments,
+ * the TTNO and x) is orthogonalised by QR into the new node tensor; the root is contracted
+ * directly. *out is created by the call: same tree and state count as x, bond of edge i
+ * min(chi, d_i * prod of its children's bonds), canonical form toward the root. With chi at
+ * least the rank of the exact product on every edge the result is H|x> up to rounding.
+ * Returns TTN_ENONFINITE for a non-finite omega. */
+ttn_status ttn_src_apply(ttn_ctx* ctx, const ttn_ttno* H, const ttn_block* x, int chi,
+                         const double* omega, ttn_block** out, ttn_precision prec);
+
 /* ---- variational fitting (Sec. II.C.2) ---------------------------------------------------- */
 
 /* For j < n_out: out_j ~ sum_k coeff[k*n_out + j] * O_k |in_k>, k < n_in, where input k is
@@ -240,21 +274,27 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
 
 /* ---- Rayleigh-Ritz without device allocation --------------------------------------------- */
 
-/* The paper has no counterpart to this call; it serves callers that cannot allocate device
- * memory while they run (work captured into or replayed from someone else's CUDA graph, a
- * device memory pool frozen after start-up, a host that budgets every byte in advance).
+/* The paper has no counterpart to this call. It serves callers that may not allocate device
+ * memory once they are running: a serving process that reserves its whole device budget at
+ * start-up, an application whose device memory pool is frozen after initialisation, or a host
+ * framework that owns the allocator and forbids allocations from libraries it calls.
  *
  * Same result as ttn_rayleigh_ritz, but Ht, Mt (m x m, row-major), theta[n] and V[m x n] are
  * DEVICE pointers owned by the caller, and the working memory is a fixed area compiled into the
- * library: about 3.7 MB of float64 per GPU, held from library load until process exit. No
- * device memory is allocated or freed by this call.
+ * library: about 3.7 MB of float64 per GPU, held from library load until process exit. The call
+ * allocates and frees no device memory (no cudaMalloc, no pool allocation).
  *   - m may not exceed TTN_RR_NOALLOC_MAX_M; larger m returns TTN_EINVAL with a message.
  *   - The first call on each device looks up the area's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device made current for the lookup); make that first call before any stream
+ *     capture on the device.
  *   - All calls on a device share the one area and it keeps the last call's contents (every
  *     value a call reads there, it has written first). Calls that overlap on the GPU (other
  *     streams, other threads) race on it: serialise them.
- * Errors as for ttn_rayleigh_ritz. The call synchronises the context's stream. */
+ *   - The eigenvalue problems are solved by a single-CTA cyclic Jacobi of at most 40 sweeps;
+ *     if either stops with sqrt(off-diagonal / total) above 1e-10 the call returns
+ *     TTN_ENOTCONV (results written).
+ * Other errors as for ttn_rayleigh_ritz. The call synchronises the context's stream: it reads
+ * the overlap spectrum on the host half way through, and again at the end. */
 #define TTN_RR_NOALLOC_MAX_M 256
 ttn_status ttn_rayleigh_ritz_noalloc(ttn_ctx* ctx, int m, const double* Ht, const double* Mt,
                                      int n, double eps, double* theta, double* V);

@@ -384,6 +384,9 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.c_len = (long long)P * g.c_pstride;
     g.max_bra = ps.max_bra;
     g.max_ket = ps.max_ket;
+    g.alg_a = l == 1;          // the ket's node tensor (permuted); later levels read T_{l-1}
+    g.alg_b = true;            // environment
+    g.alg_c = false;           // T_l
     if (level_shape_ok(g)) launch_level<T>(ctx, g);
     else launch_gemm<T>(ctx, g);
     prev_len = g.c_len;
@@ -439,6 +442,9 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.c_len = z_len;
     g.max_bra = ps.max_bra;
     g.max_ket = ps.max_ket;
+    g.alg_a = prev_mode == MODE_KET;
+    g.alg_b = false;           // folded environments (their sources count in combine_env)
+    g.alg_c = out_kind == OUT_LOCAL;
     if (level_shape_ok(g)) launch_level<T>(ctx, g);
     else launch_gemm<T>(ctx, g);
   } else {
@@ -463,6 +469,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     o.max_prefix = 0;
     for (int x : p.grp_prefix) o.max_prefix = std::max(o.max_prefix, x);
     o.n_unique_prefix = (int)std::set<int>(p.grp_prefix.begin(), p.grp_prefix.end()).size();
+    o.alg_in = prev_mode == MODE_KET;
+    o.alg_out = out_kind == OUT_LOCAL;
     launch_op_stage<T>(ctx, o);
   }
 
@@ -503,6 +511,9 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.c_len = out_len;
     g.max_bra = ps.max_bra;
     g.max_ket = ps.max_ket;
+    g.alg_a = true;            // the bra's node tensor (permuted)
+    g.alg_b = false;           // Z
+    g.alg_c = true;            // the environment
     if (closure_shape_ok(g)) launch_closure<T>(ctx, g);
     else launch_gemm<T>(ctx, g);
   } else if (out_kind == OUT_SCALAR) {

@@ -1,6 +1,7 @@
 // Host-side objects of libttn: trees, the TTNO builder, blocks of states, environment caches,
 // and the C-ABI entry points of the contraction calls.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,8 +25,16 @@ std::string ttn_fmt(const char* f, ...) {
 // ------------------------------------------------------------------------------------------------
 // device buffers
 // ------------------------------------------------------------------------------------------------
+// Allocation-failure injection (ttn_fault_inject_alloc): the number of device allocations that
+// still succeed before one fails; negative when off.
+static std::atomic<long long> g_alloc_countdown{-1};
+
 DevBuf::DevBuf(size_t n, cudaStream_t st) : bytes(n), s(st) {
   if (n == 0) return;
+  if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) == 0) {
+    g_alloc_countdown.store(-1);
+    TTN_FAIL(TTN_ENOMEM, "device allocation of %zu bytes failed: injected failure", n);
+  }
   cudaError_t e = cudaMallocAsync(&p, n, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -471,6 +480,22 @@ static ttn_block* make_block(ttn_ctx* ctx, const TreeInfo& tree, int n_states, c
   return b.release();
 }
 
+void iter_clock_start(ttn_ctx* ctx) {
+  ctx->iter_marks = -1;
+  iter_clock_mark(ctx);
+}
+
+void iter_clock_mark(ttn_ctx* ctx) {
+  const size_t i = (size_t)(ctx->iter_marks + 1);
+  while (ctx->iter_ev.size() <= i) {
+    cudaEvent_t e;
+    CUDA_CHECK(cudaEventCreate(&e));
+    ctx->iter_ev.push_back(e);
+  }
+  CUDA_CHECK(cudaEventRecord(ctx->iter_ev[i], ctx->stream));
+  ctx->iter_marks = (int)i;
+}
+
 // ------------------------------------------------------------------------------------------------
 // C ABI helpers
 // ------------------------------------------------------------------------------------------------
@@ -478,10 +503,16 @@ static ttn_block* make_block(ttn_ctx* ctx, const TreeInfo& tree, int n_states, c
 static void raise_wait_timeout(ttn_ctx* ctx) {
   if (!ctx || !ctx->h_wait) return;
   volatile unsigned* f = ctx->h_wait;
-  if (*f == 0u) return;
+  const unsigned v = *f;
+  if (v == 0u) return;
   *f = 0u;
-  TTN_FAIL(TTN_ETIMEOUT, "a bulk-copy barrier wait on the device gave up after 2 s; results of "
-                         "the work issued since the previous call are not valid");
+  if (v == TTN_WAIT_FLAG_SELFTEST)
+    TTN_FAIL(TTN_ETIMEOUT, "bounded-wait self-test: the barrier wait gave up as intended (no "
+                           "copy was in flight; the context stays usable)");
+  TTN_FAIL(TTN_ETIMEOUT, "a bulk-copy barrier wait on the device gave up after 2 s; copies may "
+                         "still have been landing when the waiting block left, so results of the "
+                         "work issued since the previous call are not valid and the context must "
+                         "be destroyed");
 }
 
 template <class F>
@@ -602,6 +633,7 @@ void ttn_destroy(ttn_ctx* ctx) {
     cudaEventDestroy(r.stop);
   }
   for (auto e : ctx->event_pool) cudaEventDestroy(e);
+  for (auto e : ctx->iter_ev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->h_wait) cudaFreeHost(ctx->h_wait);
   delete ctx;
@@ -612,6 +644,31 @@ const char* ttn_last_error(const ttn_ctx* ctx) { return ctx ? ctx->last_error.c_
 ttn_status ttn_synchronize(ttn_ctx* ctx) {
   if (!ctx) return TTN_EINVAL;
   return guarded(ctx, [&] { CUDA_CHECK(cudaStreamSynchronize(ctx->stream)); });
+}
+
+ttn_status ttn_selftest_bounded_wait(ttn_ctx* ctx, double budget_ms) {
+  if (!ctx) return TTN_EINVAL;
+  return guarded(ctx, [&] {
+    TTN_REQUIRE(ctx->device >= 0, "a host-only context has no device");
+    TTN_REQUIRE(budget_ms >= 0.001 && budget_ms <= 1000.0,
+                "budget_ms = %g outside [0.001, 1000]", budget_ms);
+    launch_wait_selftest(ctx, (unsigned long long)(budget_ms * 1e6));
+    CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+void ttn_fault_inject_alloc(long long after) { g_alloc_countdown.store(after < 0 ? -1 : after); }
+
+int ttn_iteration_times(ttn_ctx* ctx, double* ms, int max_n) {
+  if (!ctx || ctx->device < 0 || ctx->iter_marks < 1) return 0;
+  if (cudaEventSynchronize(ctx->iter_ev[ctx->iter_marks]) != cudaSuccess) return -1;
+  const int n = ctx->iter_marks;
+  for (int i = 0; i < n && i < max_n; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->iter_ev[0], ctx->iter_ev[i + 1]) != cudaSuccess) return -1;
+    ms[i] = t;
+  }
+  return n;
 }
 
 long long ttn_launch_count(const ttn_ctx* ctx) { return ctx ? ctx->launches : 0; }
@@ -1036,8 +1093,10 @@ template void gram_pairs<double>(ttn_ctx*, ttn_ttno*, const ttn_block*, const tt
 template void gram_pairs<float>(ttn_ctx*, ttn_ttno*, const ttn_block*, const ttn_block*,
                                 const std::vector<int>&, const std::vector<int>&, double*);
 
-void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
-                 double* d_mat, int ld, int prec) {
+// Writes the Gram of H into d_mat (device, leading dimension ld); returns the number of
+// non-finite entries of the result.
+unsigned gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                     double* d_mat, int ld, int prec) {
   const bool sym = bra == ket;
   std::vector<int> pb, pk;
   for (int k = 0; k < bra->n_states; ++k)
@@ -1051,7 +1110,12 @@ void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_bloc
   DevInts dpb(pb, ctx->stream), dpk(pk, ctx->stream);
   launch_scatter_gram(ctx, g.as<double>(), (int)pb.size(), dpb.get(), dpk.get(), sym ? 1 : 0,
                       d_mat, ld);
+  DevBuf cnt(sizeof(unsigned), ctx->stream);
+  launch_count_nonfinite(ctx, d_mat, bra->n_states, ket->n_states, ld, cnt.as<unsigned>());
+  unsigned bad = 0;
+  CUDA_CHECK(cudaMemcpyAsync(&bad, cnt.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
+  return bad;
 }
 
 ttn_ttno* identity_for(ttn_ctx* ctx, const TreeInfo& tree) { return cached_identity(ctx, tree); }
@@ -1116,6 +1180,7 @@ ttn_status ttn_gram(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra, cons
     TTN_REQUIRE(ld >= ket->n_states, "ld < number of ket states");
     TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision %d", (int)prec);
     const size_t mat = (size_t)bra->n_states * ld;
+    unsigned bad = 0;
     auto one = [&](ttn_ttno* H, double* out) {
       if (!out) return;
       double* dst = out;
@@ -1125,18 +1190,18 @@ ttn_status ttn_gram(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra, cons
         dst = tmp.as<double>();
       }
       CUDA_CHECK(cudaMemsetAsync(dst, 0, mat * sizeof(double), ctx->stream));
-      gram_device(ctx, H, bra, ket, dst, ld, prec);
+      bad += gram_device(ctx, H, bra, ket, dst, ld, prec);
       if (!out_on_device) {
         CUDA_CHECK(cudaMemcpyAsync(out, dst, mat * sizeof(double), cudaMemcpyDeviceToHost,
                                    ctx->stream));
         CUDA_CHECK(cudaStreamSynchronize(ctx->stream));
       }
     };
+    if (Hm) TTN_REQUIRE(Hc, "Hm requested without an operator");
     one(cached_identity(ctx, bra->tree), S);
-    if (Hm) {
-      TTN_REQUIRE(Hc, "Hm requested without an operator");
-      one(const_cast<ttn_ttno*>(Hc), Hm);
-    }
+    if (Hm) one(const_cast<ttn_ttno*>(Hc), Hm);
+    if (bad)
+      TTN_FAIL(TTN_ENONFINITE, "%u Gram entries are NaN or infinite (results written)", bad);
   });
 }
 

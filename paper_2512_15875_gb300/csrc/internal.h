@@ -34,6 +34,10 @@ std::string ttn_fmt(const char* f, ...);
   } while (0)
 #define CUDA_LAUNCH_CHECK() CUDA_CHECK(cudaGetLastError())
 
+// Values of the context's wait flag: a bulk-copy kernel gave up waiting (copies may still have
+// been landing when its CTA left), or the bounded-wait self-test ran out (nothing in flight).
+enum : unsigned { TTN_WAIT_FLAG_COPY = 1u, TTN_WAIT_FLAG_SELFTEST = 2u };
+
 // ------------------------------------------------------------------------------------------------
 // tree
 // ------------------------------------------------------------------------------------------------
@@ -101,11 +105,19 @@ struct ttn_ctx {
   double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
   bool tf32x3 = false;           // float32 calls route level stages to tensor cores
   bool capturing = false;        // a CUDA graph is being captured on the stream (no events)
-  // Set (host-mapped) by a kernel whose bounded wait on a bulk-copy barrier gave up; read and
-  // cleared by the next entry point, which then returns TTN_ETIMEOUT.
+  // Set (host-mapped) by a kernel whose bounded wait on a barrier gave up (TTN_WAIT_FLAG_*);
+  // read and cleared by the next entry point, which then returns TTN_ETIMEOUT.
   unsigned* h_wait = nullptr;
   unsigned* d_wait = nullptr;
+  // Iteration clock of the last ttn_lobpcg / ttn_inverse_iteration call: an event at its start
+  // and one after each iteration (index 0: the initial Rayleigh quotients), on the stream.
+  std::vector<cudaEvent_t> iter_ev;
+  int iter_marks = 0;
 };
+
+// Records the iteration clock's start (mark 0 .. ) on the context stream.
+void iter_clock_start(ttn_ctx* ctx);
+void iter_clock_mark(ttn_ctx* ctx);
 
 // Sets ctx->tf32x3 for the duration of one entry-point call.
 struct PrecisionScope {
@@ -288,6 +300,9 @@ struct GemmDesc {
   long long a_len, b_len, c_len;   // elements addressable from each base pointer
   int max_bra, max_ket;            // largest state index in pair_bra / pair_ket
   unsigned* wait_flag;             // device view of ttn_ctx::h_wait (set by the launcher)
+  // Which operands count as algorithmic bytes: node tensors (read once per distinct state),
+  // environments and results; intermediates of the contraction chain do not count.
+  bool alg_a, alg_b, alg_c;
 };
 
 // A list of (bra, ket) pairs on the device plus the host facts the bounds checks need.
@@ -335,7 +350,8 @@ struct OpStageDesc {
   // host-side validation
   long long a_len, z_len;
   int max_ket, max_prefix;
-  int n_unique_prefix;      // distinct T_m slices read (algorithmic bytes)
+  int n_unique_prefix;      // distinct T_m slices read
+  bool alg_in, alg_out;     // input is a node tensor / output is the contraction's result
 };
 template <class T> void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o);
 template <class T>
@@ -352,6 +368,11 @@ void launch_to_f32(ttn_ctx* ctx, const double* in, float* out, long long n);
 void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n);
 void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* pb,
                          const int* pk, int symmetric, double* out, int ld);
+// Counts the non-finite entries of rows x cols (leading dimension ld) into *d_count (device).
+void launch_count_nonfinite(ttn_ctx* ctx, const double* a, int rows, int cols, int ld,
+                            unsigned* d_count);
+// One CTA whose barrier wait cannot complete waits for budget_ns and raises the wait flag.
+void launch_wait_selftest(ttn_ctx* ctx, unsigned long long budget_ns);
 
 // ------------------------------------------------------------------------------------------------
 // engine (engine.cu)

@@ -204,6 +204,17 @@ __global__ void scatter_gram_kernel(const double* __restrict__ g, int n_pairs,
   if (symmetric) out[(long long)pk[i] * ld + pb[i]] = g[i];
 }
 
+__global__ void count_nonfinite_kernel(const double* __restrict__ a, int rows, int cols, int ld,
+                                       unsigned* __restrict__ count) {
+  const long long total = (long long)rows * cols;
+  unsigned c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    c += isfinite(a[(i / cols) * ld + i % cols]) ? 0u : 1u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 int grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 32) b = 152 * 32;
@@ -222,8 +233,10 @@ static void smem_attr(const void* fn, int bytes, int device) {
   done.insert({fn, device});
 }
 
-// Algorithmic bytes of a strided batched launch: every distinct A and B slice read once per
-// distinct base (pair / bra / ket index), every output item written once.
+// Algorithmic bytes of a strided batched launch: the operands that are node tensors,
+// environments or results of the contraction (GemmDesc::alg_*), every distinct slice once per
+// distinct base (pair / bra / ket index); intermediates of the contraction chain (T_l, Z)
+// count nothing.
 static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
   double n_ua = (double)g.hst->n_ua, n_ub = (double)g.hst->n_ub;
   if (g.hst->n_ua < 0 || g.hst->n_ub < 0) {
@@ -236,9 +249,9 @@ static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
     if (mode == MODE_KET) return std::min(g.n_pairs, g.max_ket + 1);
     return 1.0;
   };
-  const double a = bases(g.A.mode) * n_ua * g.M * g.K;
-  const double b = bases(g.B.mode) * n_ub * g.N * g.K;
-  const double c = (double)g.n_pairs * g.st.n_sub * g.M * g.N;
+  const double a = g.alg_a ? bases(g.A.mode) * n_ua * g.M * g.K : 0.0;
+  const double b = g.alg_b ? bases(g.B.mode) * n_ub * g.N * g.K : 0.0;
+  const double c = g.alg_c ? (double)g.n_pairs * g.st.n_sub * g.M * g.N : 0.0;
   return (double)elem * (a + b + c);
 }
 
@@ -375,7 +388,7 @@ void launch_permute(ttn_ctx* ctx, const T* in, T* out, long long batch, int nd, 
     a.is[k] = stride[perm[k]];
   }
   if (batch * size == 0) return;
-  LaunchScope ls(ctx, "permute", 0.0, 2.0 * sizeof(T) * batch * size);
+  LaunchScope ls(ctx, "permute", 0.0, 1.0 * sizeof(T) * batch * size);   // node tensors read
   permute_kernel<T><<<grid_for(batch * size), kThreads, 0, ctx->stream>>>(in, out, batch, size,
                                                                           a);
   CUDA_LAUNCH_CHECK();
@@ -390,7 +403,8 @@ void launch_pair_dot(ttn_ctx* ctx, const T* bra, long long bra_stride, const T* 
                   (long long)(n_pairs - 1) * z_stride + n <= z_len,
               "pair_dot bounds: bra %lld/%lld, Z %lld/%lld", (long long)max_bra * bra_stride + n,
               bra_len, (long long)(n_pairs - 1) * z_stride + n, z_len);
-  LaunchScope ls(ctx, "pair_dot", 2.0 * n * n_pairs, 2.0 * sizeof(T) * n * n_pairs);
+  LaunchScope ls(ctx, "pair_dot", 2.0 * n * n_pairs,
+                 (double)sizeof(T) * n * std::min(n_pairs, max_bra + 1) + 8.0 * n_pairs);
   pair_dot_kernel<T><<<n_pairs, kThreads, 0, ctx->stream>>>(bra, bra_stride, Z, z_stride, n,
                                                              pair_bra, out);
   CUDA_LAUNCH_CHECK();
@@ -417,6 +431,16 @@ void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n) {
   if (n == 0) return;
   LaunchScope ls(ctx, "to_f64", 0.0, 12.0 * n);
   to_f64_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
+  CUDA_LAUNCH_CHECK();
+}
+
+void launch_count_nonfinite(ttn_ctx* ctx, const double* a, int rows, int cols, int ld,
+                            unsigned* d_count) {
+  CUDA_CHECK(cudaMemsetAsync(d_count, 0, sizeof(unsigned), ctx->stream));
+  if ((long long)rows * cols == 0) return;
+  LaunchScope ls(ctx, "count_nonfinite", 0.0, 8.0 * rows * cols);
+  count_nonfinite_kernel<<<grid_for((long long)rows * cols), kThreads, 0, ctx->stream>>>(
+      a, rows, cols, ld, d_count);
   CUDA_LAUNCH_CHECK();
 }
 
@@ -548,8 +572,10 @@ void launch_op_stage(ttn_ctx* ctx, const OpStageDesc& o) {
   const long long grid = (long long)rtiles * o.n_slots * o.n_pairs;
   TTN_REQUIRE(grid <= 0x7fffffffLL, "op stage grid too large");
   const double flops = 2.0 * o.d * o.d * (double)o.rows * o.n_groups * o.n_pairs;
-  const double bytes = (double)sizeof(T) * o.n_pairs *
-                       ((double)o.n_unique_prefix * o.tsize + (double)o.n_slots * o.rows * o.d);
+  const double in_bases = o.A.mode == MODE_KET ? std::min(o.n_pairs, o.max_ket + 1) : o.n_pairs;
+  const double bytes =
+      (double)sizeof(T) * ((o.alg_in ? in_bases * o.n_unique_prefix * o.tsize : 0.0) +
+                           (o.alg_out ? (double)o.n_pairs * o.n_slots * o.rows * o.d : 0.0));
   LaunchScope ls(ctx, sizeof(T) == 8 ? "op_stage_f64" : "op_stage_f32", flops, bytes);
   switch (o.d) {
 #define TTN_OPD(k) case k: op_stage_dispatch<T, k>(ctx, o, rtiles, grid, tile); break;
@@ -680,8 +706,9 @@ void launch_combine_env(ttn_ctx* ctx, const T* E, long long e_pstride, int da, i
   const long long total = (long long)n_pairs * nG * eslice;
   if (total == 0) return;
   TTN_REQUIRE((long long)(max_w + 1) * eslice <= e_pstride, "combine bounds");
+  // algorithmic bytes: the distinct environment slices read (Et is an intermediate)
   LaunchScope ls(ctx, sizeof(T) == 8 ? "combine_env_f64" : "combine_env_f32", 2.0 * total,
-                 sizeof(T) * 2.0 * total);
+                 (double)sizeof(T) * n_pairs * (max_w + 1) * eslice);
   long long blocks = (total + kThreads - 1) / kThreads;
   if (blocks > 152 * 64) blocks = 152 * 64;
   combine_env_kernel<T><<<(int)blocks, kThreads, 0, ctx->stream>>>(E, e_pstride, da, db, Et, nG,
@@ -729,11 +756,14 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Waits for phase `parity` of the barrier; gives up after ~2 s of device time, raises the
-// context's wait flag and returns false (the caller then leaves the CTA without touching the
-// staged data).
+// Waits for phase `parity` of the barrier; gives up after budget_ns of device time (2 s for
+// the bulk-copy kernels), writes flag_value into the context's wait flag and returns false (the
+// caller then leaves the CTA without touching the staged data).
+constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
-                                          unsigned* flag) {
+                                          unsigned* flag,
+                                          unsigned long long budget_ns = kWaitBudgetNs,
+                                          unsigned flag_value = TTN_WAIT_FLAG_COPY) {
   unsigned long long t0 = 0;
   for (unsigned it = 0;; ++it) {
     unsigned done;
@@ -748,9 +778,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
       const unsigned long long now = global_ns();
       if (t0 == 0) {
         t0 = now;
-      } else if (now - t0 > 2000000000ull) {
+      } else if (now - t0 > budget_ns) {
         if (flag) {
-          *reinterpret_cast<volatile unsigned*>(flag) = 1u;
+          *reinterpret_cast<volatile unsigned*>(flag) = flag_value;
           __threadfence_system();
         }
         return false;
@@ -1057,6 +1087,26 @@ __global__ void __launch_bounds__(288) level_tma_seg_kernel(GemmDesc g, int rtil
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Self-test of the bounded wait: one thread arrives on the barrier announcing 16 bytes of
+// transfer that no copy will ever deliver, so the phase cannot complete; every thread then
+// waits with the given budget, which runs out. No copy is in flight when the CTA leaves.
+__global__ void wait_selftest_kernel(unsigned* flag, unsigned long long budget_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_expect_tx(&bar, 16u);
+  mbar_wait(&bar, 0, flag, budget_ns, TTN_WAIT_FLAG_SELFTEST);
+}
+
+void launch_wait_selftest(ttn_ctx* ctx, unsigned long long budget_ns) {
+  LaunchScope ls(ctx, "wait_selftest", 0.0, 0.0);
+  wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(ctx->d_wait, budget_ns);
+  CUDA_LAUNCH_CHECK();
 }
 
 // Segmented level stage, warp-specialised (float32 SIMT compute, slices stored [b][a] with

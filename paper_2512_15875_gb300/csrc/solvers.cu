@@ -25,8 +25,8 @@ ttn_ttno* identity_for(ttn_ctx* ctx, const TreeInfo& tree);
 template <class T>
 void gram_pairs(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
                 const std::vector<int>& pb, const std::vector<int>& pk, double* d_out);
-void gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
-                 double* d_mat, int ld, int prec);
+unsigned gram_device(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* bra, const ttn_block* ket,
+                     double* d_mat, int ld, int prec);
 
 namespace {
 
@@ -385,8 +385,11 @@ __global__ void mr_step_vectors(const double* sc, T* x, T* v, T* vp, T* w1, T* w
 }
 
 // ---- Rayleigh-Ritz: cyclic Jacobi (round-robin parallel ordering), one CTA, float64 ---------
+// off_out (may be NULL) receives sqrt(off-diagonal / total) of A's squared entries when the
+// kernel returns: at most tol when it stopped on the tolerance, the reached value after
+// max_sweeps otherwise.
 __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int m, int max_sweeps,
-                                                      double tol) {
+                                                      double tol, double* off_out) {
   extern __shared__ double sh[];
   const int mp = m + (m & 1);
   const int npairs = mp / 2;
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x)
     V[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
   __syncthreads();
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+  for (int sweep = 0; sweep <= max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
       const double a = A[idx];
@@ -407,7 +410,11 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
-    if (off <= tol * tol * tot) break;
+    const bool done = off <= tol * tol * tot;
+    if (done || sweep == max_sweeps) {
+      if (off_out && threadIdx.x == 0) off_out[0] = tot > 0.0 ? sqrt(off / tot) : 0.0;
+      break;
+    }
     for (int r = 0; r < mp - 1; ++r) {
       for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
         int p, q;
@@ -1268,7 +1275,7 @@ template <class F>
 static ttn_status guarded_s(ttn_ctx* ctx, F&& f) {
   try {
     ttn_status s = f();
-    ctx->last_error.clear();
+    if (s == TTN_OK) ctx->last_error.clear();
     return s;
   } catch (const TtnError& e) {
     ctx->last_error = e.msg;
@@ -1304,6 +1311,7 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     if (s != TTN_OK) TTN_FAIL(s, "%s", ctx->last_error.c_str());
     return std::unique_ptr<ttn_block>(b);
   };
+  iter_clock_start(ctx);
   normalize_states<T>(ctx, x, prec);
   std::vector<double> lam(n);
   {
@@ -1317,6 +1325,7 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     for (int j = 0; j < n; ++j) lam[j] = h[j] / s[j];
   }
   if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist);
+  iter_clock_mark(ctx);
   auto R = new_block(n), Y = new_block(n), P = new_block(n), Xn = new_block(n), Pn = new_block(n);
   bool have_p = false;
   const double rr_eps = prec == TTN_FP64 ? 1e-12 : 1e-6;
@@ -1375,11 +1384,13 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
     {
       PhaseScope ph(ctx, "gram_H");
-      gram_device(ctx, H, S.get(), S.get(), Ht.as<double>(), m, prec);
+      if (gram_device(ctx, H, S.get(), S.get(), Ht.as<double>(), m, prec))
+        TTN_FAIL(TTN_ENONFINITE, "LOBPCG iteration %d: non-finite <s_k|H|s_l>", it);
     }
     {
       PhaseScope ph(ctx, "gram_S");
-      gram_device(ctx, Id, S.get(), S.get(), Mt.as<double>(), m, prec);
+      if (gram_device(ctx, Id, S.get(), S.get(), Mt.as<double>(), m, prec))
+        TTN_FAIL(TTN_ENONFINITE, "LOBPCG iteration %d: non-finite <s_k|s_l>", it);
     }
     DevBuf th((size_t)n * sizeof(double), st), V((size_t)m * n * sizeof(double), st);
     {
@@ -1437,7 +1448,129 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     }
     lam = hth;
     if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist + (size_t)it * n);
+    iter_clock_mark(ctx);
   }
+  CUDA_CHECK(cudaStreamSynchronize(st));
+}
+
+// Successive randomized compression (Sec. II.C.1, Figs. random tensor and src): y ~ H x for
+// every state of x with sketch dimension chi. The Khatri-Rao sketch columns are chi product
+// states (bond one) whose node tensors are the columns c_k^(i) of Omega^(i); their top-down
+// environments with H and x (pair s * chi + k) sketch everything outside an edge. Leaves to
+// root: the local sketch Y_i[k][s_children][p] is the H_eff-type contraction of node i with the
+// parent edge's down sketch (column index k as its bra bond) and the children's residual
+// environments R_c = <y|H|x>; its QR over (s_children, p) x k gives the new node tensor (the
+// identity when there are at most chi rows) and R_i; the root contracts directly. y's bonds
+// are min(chi, d_i * prod of its children's bonds) and must be set on entry.
+template <class T>
+static void src_impl(ttn_ctx* ctx, ttn_ttno* H, const ttn_block* x, int chi,
+                     const std::vector<std::vector<double>>& omega, ttn_block* y) {
+  const TreeInfo& tr = x->tree;
+  const int n = x->n_states;
+  cudaStream_t st = ctx->stream;
+  if (n == 0) return;
+  // the chi sketch columns as a block of product states
+  ttn_block* skp = nullptr;
+  {
+    ttn_tree tmp;
+    tmp.ctx = ctx;
+    tmp.info = tr;
+    std::vector<int> ones(tr.n, 1);
+    ttn_status cs = ttn_block_create(ctx, &tmp, chi, ones.data(), &skp);
+    if (cs != TTN_OK) TTN_FAIL(cs, "%s", ctx->last_error.c_str());
+  }
+  std::unique_ptr<ttn_block> sk(skp);
+  for (int t = 0; t < tr.n; ++t) {
+    const int d = tr.d(t);
+    std::vector<double> h((size_t)chi * d, 1.0);
+    if (tr.phys[t] > 0)
+      for (int k = 0; k < chi; ++k)
+        for (int p = 0; p < d; ++p) h[(size_t)k * d + p] = omega[t][(size_t)p * chi + k];
+    CUDA_CHECK(cudaMemcpyAsync(sk->node64(t), h.data(), h.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, st));
+    CUDA_CHECK(cudaStreamSynchronize(st));
+  }
+  sk->touch();
+  std::vector<int> pb((size_t)n * chi), pk((size_t)n * chi), id(n);
+  for (int s = 0; s < n; ++s) {
+    id[s] = s;
+    for (int k = 0; k < chi; ++k) {
+      pb[(size_t)s * chi + k] = k;
+      pk[(size_t)s * chi + k] = s;
+    }
+  }
+  EnvCache<T> sketch;
+  sketch.init(ctx, H, sk.get(), x, pb, pk);
+  DevVec did_b, did_k;
+  PairSet ps = make_pairs(id, id, did_b, did_k, st);
+  std::vector<DevBuf> R(tr.n);
+  for (int t : tr.post) {
+    const int nl = tr.nlegs(t);
+    std::vector<const T*> env(nl, nullptr);
+    std::vector<int> da(nl);
+    const int off = t == tr.root ? 0 : 1;
+    for (int m = off; m < nl; ++m) {
+      const int c = tr.legs[t][m];
+      env[m] = R[c].as<T>();
+      da[m] = y->bond[c];
+    }
+    if (t == tr.root) {
+      T* out = work_node<T>(y, t);
+      node_op<T>(ctx, H, t, -1, nullptr, x, ps, env, da, out, (long long)n * y->size[t],
+                 OUT_LOCAL);
+      continue;
+    }
+    const int Dw = H->wbond[t], Db = x->bond[t];
+    DevBuf E0((size_t)n * Dw * chi * Db * sizeof(T), st);
+    {
+      const int dims[4] = {n, chi, Dw, Db}, perm[4] = {0, 2, 1, 3};
+      launch_permute<T>(ctx, sketch.get_down(t), E0.as<T>(), 1, 4, dims, perm);
+    }
+    env[0] = E0.as<T>();
+    da[0] = chi;
+    long long rows = tr.d(t);
+    for (int m = 1; m < nl; ++m) rows *= da[m];
+    DevBuf Y((size_t)n * chi * rows * sizeof(T), st);
+    node_op<T>(ctx, H, t, -1, nullptr, x, ps, env, da, Y.p, (long long)n * chi * rows, OUT_LOCAL);
+    T* node = work_node<T>(y, t);
+    TTN_REQUIRE(y->size[t] == rows * y->bond[t], "src: output bonds do not match node %d", t);
+    if (rows <= chi) {
+      std::vector<T> eye((size_t)n * rows * rows, T(0));
+      for (int s = 0; s < n; ++s)
+        for (long long r = 0; r < rows; ++r) eye[(size_t)s * rows * rows + r * rows + r] = T(1);
+      CUDA_CHECK(cudaMemcpyAsync(node, eye.data(), eye.size() * sizeof(T),
+                                 cudaMemcpyHostToDevice, st));
+      CUDA_CHECK(cudaStreamSynchronize(st));
+    } else {
+      TTN_REQUIRE(chi <= 64, "src: chi = %d above 64 is not supported", chi);
+      const long long msz = rows * chi;
+      DevBuf M((size_t)n * msz * sizeof(T), st), Q((size_t)n * msz * sizeof(T), st),
+          Rq((size_t)n * chi * chi * sizeof(T), st);
+      const int d1[2] = {chi, (int)rows}, p1[2] = {1, 0};
+      launch_permute<T>(ctx, Y.as<T>(), M.as<T>(), n, 2, d1, p1);
+      {
+        LaunchScope ls(ctx, sizeof(T) == 8 ? "householder_qr_f64" : "householder_qr_f32",
+                       4.0 * rows * chi * chi * n, 4.0 * sizeof(T) * msz * n);
+        const size_t smem = 2 * (size_t)msz * sizeof(T);
+        const bool on_chip = smem <= 200 * 1024;
+        if (on_chip)
+          CUDA_CHECK(cudaFuncSetAttribute(householder_qr_kernel<T>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
+        householder_qr_kernel<T><<<n, kT, on_chip ? smem : 0, st>>>(
+            M.as<T>(), Q.as<T>(), Rq.as<T>(), (int)rows, chi, msz, on_chip ? 1 : 0);
+        CUDA_LAUNCH_CHECK();
+      }
+      const int d2[2] = {(int)rows, chi}, p2[2] = {1, 0};
+      launch_permute<T>(ctx, Q.as<T>(), node, n, 2, d2, p2);
+    }
+    std::vector<const T*> renv(nl, nullptr);
+    for (int m = 1; m < nl; ++m) renv[m] = env[m];
+    const long long esz = (long long)n * Dw * y->bond[t] * Db;
+    R[t] = DevBuf((size_t)esz * sizeof(T), st);
+    node_op<T>(ctx, H, t, 0, y, x, ps, renv, {}, R[t].p, esz, OUT_ENV);
+  }
+  commit<T>(y);
   CUDA_CHECK(cudaStreamSynchronize(st));
 }
 
@@ -1487,9 +1620,11 @@ static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int 
     CUDA_CHECK(cudaStreamSynchronize(st));
     return h;
   };
+  iter_clock_start(ctx);
   normalize_states<T>(ctx, x, prec);
   std::vector<double> lam = diag(H, x);
   if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist);
+  iter_clock_mark(ctx);
   auto Y = new_block(n), Xn = new_block(n);
   const double rr_eps = prec == TTN_FP64 ? 1e-12 : 1e-6;
   for (int it = 1; it <= n_iter; ++it) {
@@ -1523,8 +1658,9 @@ static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int 
           th((size_t)m * sizeof(double), st), V((size_t)m * m * sizeof(double), st);
       CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
       CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
-      gram_device(ctx, H, Yc.get(), Yc.get(), Ht.as<double>(), m, prec);
-      gram_device(ctx, Id, Yc.get(), Yc.get(), Mt.as<double>(), m, prec);
+      if (gram_device(ctx, H, Yc.get(), Yc.get(), Ht.as<double>(), m, prec) +
+          gram_device(ctx, Id, Yc.get(), Yc.get(), Mt.as<double>(), m, prec))
+        TTN_FAIL(TTN_ENONFINITE, "inverse iteration %d: non-finite block Gram", it);
       rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), m, rr_eps, th.as<double>(),
                            V.as<double>());
       std::vector<double> hth(m), hV((size_t)m * m);
@@ -1569,6 +1705,7 @@ static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int 
     if (cs != TTN_OK) TTN_FAIL(cs, "copy");
     lam = lam_n;
     if (eig_hist) std::copy(lam.begin(), lam.end(), eig_hist + (size_t)it * n);
+    iter_clock_mark(ctx);
   }
   CUDA_CHECK(cudaStreamSynchronize(st));
 }
@@ -1576,18 +1713,21 @@ static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int 
 // ------------------------------------------------------------------------------------------------
 // Rayleigh-Ritz without device allocation.
 //
-// Some callers cannot allocate device memory while they run: code inside a CUDA graph being
-// captured or replayed by someone else, a memory pool that is frozen after start-up, or a host
-// that budgets every byte up front. For them ttn_rayleigh_ritz_noalloc works in a fixed working
-// area that lives for the life of the process: the file-scope array below. Its size bounds the
-// problem (m <= TTN_RR_NOALLOC_MAX_M); every GPU that loads the library holds it until exit.
+// Some callers may not allocate device memory once they are running: a serving process that
+// reserves its device budget at start-up, a memory pool that is frozen after initialisation, a
+// host framework that owns the allocator. For them ttn_rayleigh_ritz_noalloc works in a fixed
+// working area that lives for the life of the process: the file-scope array below. Its size
+// bounds the problem (m <= TTN_RR_NOALLOC_MAX_M); every GPU that loads the library holds it
+// until exit.
 // ------------------------------------------------------------------------------------------------
 namespace {
 
 constexpr int kRRMaxM = TTN_RR_NOALLOC_MAX_M;
 // A, U, Us, X, HX, Hp, Y (m x m each) + mu, th (m each) + keep indices (m ints, stored in m
-// doubles)
-constexpr size_t kRRScratchDoubles = 7ull * kRRMaxM * kRRMaxM + 3ull * kRRMaxM;
+// doubles) + the final off-diagonal ratios of the two Jacobi solves (padded to 8 doubles)
+constexpr size_t kRRScratchDoubles = 7ull * kRRMaxM * kRRMaxM + 3ull * kRRMaxM + 8;
+// A Jacobi solve whose final sqrt(off-diagonal / total) is above this did not converge.
+constexpr double kRRJacobiOffBound = 1e-10;
 static __device__ __align__(256) double g_rr_scratch[kRRScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -1674,7 +1814,10 @@ ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
                                       minres_max, minres_tol)
                    : als_impl<float>(ctx, const_cast<ttn_ttno*>(H), s, rhs, y, n_sweeps,
                                      minres_max, minres_tol);
-    return hit ? TTN_ENOTCONV : TTN_OK;
+    if (!hit) return TTN_OK;
+    ctx->last_error = "a local MINRES solve reached minres_max before its tolerance (results "
+                      "written)";
+    return TTN_ENOTCONV;
   });
 }
 
@@ -1717,7 +1860,10 @@ ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
     else
       lobpcg_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
                          minres_max, minres_tol, fit_sweeps, prec, eig_hist, hit);
-    return hit ? TTN_ENOTCONV : TTN_OK;
+    if (!hit) return TTN_OK;
+    ctx->last_error = "a local MINRES solve reached minres_max before its tolerance (results "
+                      "written)";
+    return TTN_ENOTCONV;
   });
 }
 
@@ -1742,7 +1888,54 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
       inverse_iteration_impl<float>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, cluster_gap,
                                     als_sweeps, minres_max, minres_tol, fit_sweeps, prec,
                                     rq_hist, hit);
-    return hit ? TTN_ENOTCONV : TTN_OK;
+    if (!hit) return TTN_OK;
+    ctx->last_error = "a local MINRES solve reached minres_max before its tolerance (results "
+                      "written)";
+    return TTN_ENOTCONV;
+  });
+}
+
+ttn_status ttn_src_apply(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* x, int chi,
+                         const double* omega, ttn_block** out, ttn_precision prec) {
+  if (!ctx || !Hc || !x || !omega || !out) return TTN_EINVAL;
+  *out = nullptr;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
+    ttn_ttno* H = const_cast<ttn_ttno*>(Hc);
+    const TreeInfo& tr = x->tree;
+    TTN_REQUIRE(H->tree.same_shape(tr), "TTNO and block live on different trees");
+    TTN_REQUIRE(chi >= 1 && chi <= 64, "chi = %d outside [1, 64]", chi);
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3,
+                "unknown precision %d", (int)prec);
+    std::vector<std::vector<double>> om(tr.n);
+    long long o = 0;
+    for (int t = 0; t < tr.n; ++t) {
+      if (tr.phys[t] <= 0) continue;
+      om[t].assign(omega + o, omega + o + (long long)tr.phys[t] * chi);
+      o += (long long)tr.phys[t] * chi;
+    }
+    for (long long i = 0; i < o; ++i)
+      if (!std::isfinite(omega[i])) TTN_FAIL(TTN_ENONFINITE, "omega[%lld] is not finite", i);
+    std::vector<int> bond(tr.n, 1);
+    for (int t : tr.post) {
+      if (t == tr.root) continue;
+      long long rows = tr.d(t);
+      for (int c : tr.children[t]) rows *= bond[c];
+      bond[t] = (int)std::min<long long>(chi, rows);
+    }
+    ttn_block* yb = nullptr;
+    {
+      ttn_tree tmp;
+      tmp.ctx = ctx;
+      tmp.info = tr;
+      ttn_status cs = ttn_block_create(ctx, &tmp, x->n_states, bond.data(), &yb);
+      if (cs != TTN_OK) TTN_FAIL(cs, "%s", ctx->last_error.c_str());
+    }
+    std::unique_ptr<ttn_block> guard(yb);
+    if (prec == TTN_FP64) src_impl<double>(ctx, H, x, chi, om, yb);
+    else src_impl<float>(ctx, H, x, chi, om, yb);
+    *out = guard.release();
+    return TTN_OK;
   });
 }
 
@@ -1777,19 +1970,22 @@ ttn_status ttn_rayleigh_ritz_noalloc(ttn_ctx* ctx, int m, const double* Ht, cons
     double* mu = Y + mm;
     double* th = mu + m;
     int* keep = reinterpret_cast<int*>(th + m);
-    auto eig = [&](double* Ain, int k, double* evals, double* Vout) {
+    double* offr = th + 2 * m;
+    auto eig = [&](double* Ain, int k, double* evals, double* Vout, double* off_out) {
       symmetrize_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(Ain, k);
       const int kp = k + (k & 1);
       const size_t sh = (size_t)kp * sizeof(double) + (size_t)kp * sizeof(int) + 64;
-      jacobi_kernel<<<1, 1024, sh, st>>>(Ain, U, k, 40, 1e-15);
+      jacobi_kernel<<<1, 1024, sh, st>>>(Ain, U, k, 40, 1e-15, off_out);
       sort_eig_kernel<<<1, 256, k * sizeof(int), st>>>(Ain, U, k, evals, Vout);
       ctx->launches += 3;
       CUDA_LAUNCH_CHECK();
     };
     CUDA_CHECK(cudaMemcpyAsync(A, Mt, mm * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    eig(A, m, mu, Us);
+    eig(A, m, mu, Us, offr);
     double hmu[kRRMaxM];
+    double hoff[2] = {0.0, 0.0};
     CUDA_CHECK(cudaMemcpyAsync(hmu, mu, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_CHECK(cudaMemcpyAsync(hoff, offr, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
     double mx = hmu[0];
     for (int i = 0; i < m; ++i) {
@@ -1807,13 +2003,20 @@ ttn_status ttn_rayleigh_ritz_noalloc(ttn_ctx* ctx, int m, const double* Ht, cons
     small_gemm_kernel<<<grid_of((long long)k * k), kT, 0, st>>>(X, 1, k, HX, k, 1, Hp, k, k, m);
     ctx->launches += 3;
     CUDA_LAUNCH_CHECK();
-    eig(Hp, k, th, Y);
+    eig(Hp, k, th, Y, offr + 1);
     small_gemm_kernel<<<grid_of((long long)m * n), kT, 0, st>>>(X, k, 1, Y, k, 1, V, m, n, k);
     fix_sign_kernel<<<(n + 127) / 128, 128, 0, st>>>(V, m, n);
     ctx->launches += 2;
     CUDA_LAUNCH_CHECK();
     CUDA_CHECK(cudaMemcpyAsync(theta, th, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CUDA_CHECK(cudaMemcpyAsync(hoff + 1, offr + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
     CUDA_CHECK(cudaStreamSynchronize(st));
+    if (!(hoff[0] <= kRRJacobiOffBound && hoff[1] <= kRRJacobiOffBound)) {
+      ctx->last_error = ttn_fmt("Jacobi eigensolver stopped at off-diagonal ratios %.3g (overlap) "
+                                "and %.3g (projected H), above %.0e (results written)",
+                                hoff[0], hoff[1], kRRJacobiOffBound);
+      return TTN_ENOTCONV;
+    }
     return TTN_OK;
   });
 }

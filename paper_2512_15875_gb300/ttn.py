@@ -68,6 +68,10 @@ _SIGS = {
     "ttn_lobpcg": (_I, [_P, _P, _P, _I, _D, _I, _I, _D, _I, _I, _DP]),
     "ttn_rayleigh_ritz_noalloc": (_I, [_P, _I, _P, _P, _I, _D, _P, _P]),
     "ttn_inverse_iteration": (_I, [_P, _P, _P, _I, _D, _I, _I, _D, _I, _I, _DP]),
+    "ttn_src_apply": (_I, [_P, _P, _P, _I, _DP, C.POINTER(_P), _I]),
+    "ttn_selftest_bounded_wait": (_I, [_P, _D]),
+    "ttn_iteration_times": (_I, [_P, _DP, _I]),
+    "ttn_fault_inject_alloc": (None, [_LL]),
 }
 
 
@@ -195,6 +199,25 @@ def ttn_create(device=0, stream=None) -> Context:
     if st != 0:
         raise TTNError(st, "ttn_create failed")
     return Context(p.value)
+
+
+def ttn_selftest_bounded_wait(ctx, budget_ms=1.0):
+    """Returns the status of a barrier wait that is made to run out (TTN_ETIMEOUT = 6)."""
+    return load().ttn_selftest_bounded_wait(ctx.ptr, float(budget_ms))
+
+
+def ttn_iteration_times(ctx, max_n=100000):
+    """ms from the start of the last ttn_lobpcg / ttn_inverse_iteration call to the end of each
+    iteration (index 0: the initial Rayleigh quotients)."""
+    out = np.zeros(max_n)
+    n = load().ttn_iteration_times(ctx.ptr, _dp(out), int(max_n))
+    if n < 0:
+        raise TTNError(3, "ttn_iteration_times: CUDA error")
+    return out[:min(n, max_n)]
+
+
+def ttn_fault_inject_alloc(after):
+    load().ttn_fault_inject_alloc(int(after))
 
 
 def ttn_synchronize(ctx):
@@ -392,6 +415,20 @@ def ttn_apply_block(ctx, H, block, prec="fp64") -> Block:
     return b
 
 
+def ttn_src_apply(ctx, H, x, chi, omega, prec="fp64") -> Block:
+    """omega: per-node d_i x chi matrices (None for auxiliary nodes), as inputs.src_sketch
+    draws them. Returns the new block (bonds min(chi, d_i * prod of children's bonds))."""
+    flat = np.ascontiguousarray(np.concatenate(
+        [np.asarray(o, dtype=np.float64).ravel() for o in omega if o is not None]))
+    p = _P()
+    ctx.check(load().ttn_src_apply(ctx.ptr, H.ptr, x.ptr, int(chi), _dp(flat), C.byref(p),
+                                   _prec(prec)))
+    b = Block(p.value, ctx)
+    b.n_states = x.n_states
+    b.n_nodes = x.n_nodes
+    return b
+
+
 def ttn_recompress(ctx, coeff, ops, blocks, in_state, out, n_sweeps=2, prec="fp64"):
     """coeff: (n_in, n_out) array; ops/blocks: per-input TTNO (or None) and Block."""
     coeff = np.ascontiguousarray(coeff, dtype=np.float64)
@@ -426,9 +463,13 @@ def ttn_rayleigh_ritz(ctx, Ht, Mt, n, eps=1e-12):
 
 def ttn_rayleigh_ritz_noalloc(ctx, m, Ht_ptr, Mt_ptr, n, eps, theta_ptr, V_ptr):
     """Device-pointer variant that allocates no device memory (see include/ttn.h). All four
-    pointers are device addresses (ints) owned by the caller."""
-    ctx.check(load().ttn_rayleigh_ritz_noalloc(ctx.ptr, int(m), Ht_ptr, Mt_ptr, int(n),
-                                               float(eps), theta_ptr, V_ptr))
+    pointers are device addresses (ints) owned by the caller. Returns the status: 0, or 5
+    (TTN_ENOTCONV, results written) when an eigensolve stopped short of convergence."""
+    st = load().ttn_rayleigh_ritz_noalloc(ctx.ptr, int(m), Ht_ptr, Mt_ptr, int(n), float(eps),
+                                          theta_ptr, V_ptr)
+    if st not in (0, 5):
+        ctx.check(st)
+    return st
 
 
 def ttn_lobpcg(ctx, H, x, n_iter, shift_offset, als_sweeps=2, minres_max=10, minres_tol=1e-5,

@@ -6,6 +6,8 @@ GPU Gram (built with the library's compressed TTNO) against the oracle's environ
 with its own, independently constructed state-diagram TTNO; both represent the same Hamiltonian
 (Eq. sum_of_tp), so agreement checks the builder and the kernels together.
 FP64 1e-11 relative to the largest diagonal entry; FP32 2e-5."""
+import os
+
 import numpy as np
 import pytest
 
@@ -45,3 +47,93 @@ def test_full_size_gram_sampled(T, ctx, name, prec):
         a, c = [x[i] for x in blk], [x[j] for x in blk]
         assert abs(Hm[i, j] - N.expectation(w.tree, otn, a, c)) <= tol * scale_h, (i, j)
         assert abs(S[i, j] - N.overlap(w.tree, a, c)) <= tol * scale_s, (i, j)
+
+
+# --- element-wise parity at the benchmark size ------------------------------------------------
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_gram_252.npz")
+TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-5}
+
+
+def _c2_gold_block(name):
+    """The seeded blocks of tests/golden/make_c2_gram.py (same generator calls)."""
+    w = I.make_workload("c2")
+    g = np.load(GOLD)
+    n = int(g["n_states"])
+    if name == "prod":
+        blk = I.initial_block(w.tree, w.ham, w.bonds, n, seed=0, noise=1e-2)
+    else:
+        blk = I.random_block(w.tree, w.bonds, n, seed=7, scale=float(g["rand_scale"]))
+    return w, blk, g
+
+
+@pytest.mark.parametrize("workspace_gb", [None, "1.5"])
+@pytest.mark.parametrize("block", ["prod", "rand"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_c2_gram_every_entry_matches_the_oracle(T, ctx, prec, block, workspace_gb, monkeypatch):
+    """All 31 878 pairs of the 252-state subspace of the 12-mode QFF (fork-4, D = 24) against the
+    oracle's values stored by tests/golden/make_c2_gram.py, for near-product and dense random
+    states; with a 1.5 GB workspace the pairs run in many chunks with a ragged last one."""
+    if workspace_gb is not None:
+        if prec != "fp32":
+            pytest.skip("chunking is checked once, in float32")
+        monkeypatch.setenv("TTN_WORKSPACE_GB", workspace_gb)
+    w, blk, g = _c2_gold_block(block)
+    th = T.ttn_tree_create(ctx, w.tree)
+    H, _ = T.ttn_build_ttno(ctx, th, w.ham.flat(w.tree))
+    b = T.block_from_arrays(ctx, th, w.bonds, blk)
+    S, Hm = T.ttn_gram(ctx, H, b, b, prec=prec)
+    iu = np.triu_indices(int(g["n_states"]))
+    ref_h, ref_s = g[f"{block}_H"], g[f"{block}_S"]
+    n = int(g["n_states"])
+    diag = np.arange(n) * n - np.arange(n) * (np.arange(n) - 1) // 2   # (k, k) in the triangle
+    scale_h, scale_s = np.abs(ref_h[diag]).max(), np.abs(ref_s[diag]).max()
+    assert np.abs(Hm[iu] - ref_h).max() <= TOL[prec] * scale_h
+    assert np.abs(S[iu] - ref_s).max() <= TOL[prec] * scale_s
+
+
+def _import_ttno(T, ctx, th, tree, otn):
+    ops, entries = [], []
+    for node in range(tree.n_nodes):
+        for wv, op, c in otn.entries[node]:
+            entries.append((node, tuple(wv), len(ops), c))
+            ops.append((node, op))
+    return T.ttn_ttno_create(ctx, th, otn.wbond, ops, entries)
+
+
+@pytest.mark.parametrize("name,nodes", [("c2", (1, 5)), ("c5", (1,))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_full_size_environments_and_heff(T, ctx, name, nodes, prec):
+    """Environments on every leg of a backbone node (two children, no physical leg) and of a
+    chain node (one child and a physical leg) of the 12-mode QFF on the fork-4 tree at D = 24,
+    and of a node with a parent, two children and a physical leg of the all-physical tree at
+    D = 32, for three bra/ket pairs, element by element; and H_eff at those nodes. The oracle's
+    state-diagram TTNO is imported so both sides use the same operator bond basis."""
+    w = I.make_workload(name)
+    tree = w.tree
+    th = T.ttn_tree_create(ctx, tree)
+    otn = N.build_ttno(tree, w.ham)
+    H = _import_ttno(T, ctx, th, tree, otn)
+    blk = I.initial_block(tree, w.ham, w.bonds, 3, seed=3, noise=1e-2)
+    b = T.block_from_arrays(ctx, th, w.bonds, blk)
+    pb, pk = [0, 1, 2], [1, 2, 2]
+    envs = T.ttn_envs_create(ctx, th)
+    T.ttn_env_update(ctx, H, b, b, pb, pk, 2, envs, prec)
+    tol = TOL[prec]
+    for p, (i, j) in enumerate(zip(pb, pk)):
+        up, down = N.environments(tree, otn, [x[i] for x in blk], [x[j] for x in blk])
+        for t in nodes:
+            for e in [t] + tree.children(t):
+                for direction, ref in ((0, up[e]), (1, down[e])):
+                    ref = np.transpose(ref, (1, 0, 2))      # oracle [a,w,b] -> library [w,a,b]
+                    got = T.ttn_envs_get(envs, e, direction, p, ref.shape)
+                    assert np.abs(got - ref).max() <= tol * np.abs(ref).max(), (t, e, direction)
+    envs_d = T.ttn_envs_create(ctx, th)
+    T.ttn_env_update(ctx, H, b, b, [0, 1, 2], [0, 1, 2], 2, envs_d, prec)
+    bY = T.ttn_block_create(ctx, th, 3, w.bonds)
+    for t in nodes:
+        T.ttn_heff_apply(ctx, H, envs_d, t, b, bY, prec=prec)
+        got = T.ttn_block_get(bY, -1, t).reshape((3,) + I.node_shape(tree, w.bonds, t))
+        for s in range(3):
+            ref = N.heff_apply(tree, otn, t, [x[s] for x in blk], blk[t][s])
+            assert np.abs(got[s] - ref).max() <= 10 * tol * np.abs(ref).max(), (t, s)
