@@ -135,6 +135,15 @@ ttn_status ttn_build_ttno(ttn_ctx* ctx, const ttn_tree* tree, int n_ops, const i
                           const double* coeff, const int* term_offset, const int* term_op_ids,
                           double tol, ttn_ttno** out, int* bond_dims_out);
 
+/* Lower bound on the operator bond of each edge (the TTNO paragraph of Sec. II.A.3): rank_out[i]
+ * for the edge (i, parent(i)) is the numerical rank (pivoted QR, float64, relative tolerance
+ * 1e-12) of the matrix of term coefficients indexed by the term's operator string on the subtree
+ * of i and its string on the rest of the tree, the smallest bond any exact TTNO of H can have
+ * there when distinct operator strings are linearly independent. 1 at the root; -1 on every
+ * edge of a TTNO made by ttn_ttno_create (no terms known). Compare with bond_dims_out of
+ * ttn_build_ttno. */
+ttn_status ttn_ttno_rank_bounds(const ttn_ttno* H, int* rank_out);
+
 /* Create a TTNO from explicit entries (no arithmetic): operator bonds wbond[n_nodes] (root
  * ignored), an op table as in ttn_build_ttno, and n_entries entries with entry_node[e],
  * w-tuple entry_w[e*TTN_MAX_LEGS + m] for the node's legs m in tensor order, op index
@@ -167,7 +176,8 @@ ttn_status ttn_block_get(const ttn_block* b, int state, int node, double* host, 
 /* Tensor size of `node` and the device address of its [state][tensor] slab. */
 ttn_status ttn_block_node_info(const ttn_block* b, int node, long long* size,
                                double** device_ptr);
-/* dst state j := src state src_states[j] for j < n (same tree and bonds). */
+/* dst state j := src state src_states[j] for j < n (same tree and bonds, distinct blocks);
+ * one gather launch per node. */
 ttn_status ttn_block_copy_states(ttn_block* dst, const ttn_block* src, int n,
                                  const int* src_states);
 

@@ -10,6 +10,7 @@
 #include <map>
 #include <numeric>
 #include <set>
+#include <tuple>
 
 #include "internal.h"
 
@@ -243,6 +244,97 @@ static void copy_op_table(ttn_ttno* H, int n_ops, const int* op_site, const long
     H->op_data.insert(H->op_data.end(), op_data + op_offset[o], op_data + op_offset[o + 1]);
     H->op_off.push_back((long long)H->op_data.size());
   }
+}
+
+// Numerical rank of a dense rows x cols matrix (row-major, destroyed): Householder QR with
+// column pivoting in float64; columns whose remaining norm falls to tol * (largest column norm)
+// or below end the factorisation.
+static int pivoted_qr_rank(std::vector<double>& A, int rows, int cols, double tol) {
+  std::vector<double> cn(cols, 0.0);
+  for (int j = 0; j < cols; ++j)
+    for (int i = 0; i < rows; ++i) cn[j] += A[(size_t)i * cols + j] * A[(size_t)i * cols + j];
+  double first = 0.0;
+  int r = 0;
+  const int kmax = std::min(rows, cols);
+  for (int k = 0; k < kmax; ++k) {
+    int p = k;
+    for (int j = k + 1; j < cols; ++j)
+      if (cn[j] > cn[p]) p = j;
+    if (p != k) {
+      std::swap(cn[p], cn[k]);
+      for (int i = 0; i < rows; ++i) std::swap(A[(size_t)i * cols + p], A[(size_t)i * cols + k]);
+    }
+    double nrm = 0.0;   // recomputed from the trailing column (no downdating drift)
+    for (int i = k; i < rows; ++i) nrm += A[(size_t)i * cols + k] * A[(size_t)i * cols + k];
+    nrm = std::sqrt(nrm);
+    if (k == 0) first = nrm;
+    if (nrm <= tol * first || nrm == 0.0) break;
+    ++r;
+    const double a0 = A[(size_t)k * cols + k];
+    const double alpha = a0 >= 0.0 ? -nrm : nrm;
+    std::vector<double> v(rows - k);
+    v[0] = a0 - alpha;
+    for (int i = k + 1; i < rows; ++i) v[i - k] = A[(size_t)i * cols + k];
+    double vv = 0.0;
+    for (double x : v) vv += x * x;
+    if (vv == 0.0) continue;
+    for (int j = k; j < cols; ++j) {
+      double dot = 0.0;
+      for (int i = k; i < rows; ++i) dot += v[i - k] * A[(size_t)i * cols + j];
+      const double f = 2.0 * dot / vv;
+      for (int i = k; i < rows; ++i) A[(size_t)i * cols + j] -= f * v[i - k];
+    }
+    for (int j = k + 1; j < cols; ++j) {
+      double s2 = 0.0;
+      for (int i = k + 1; i < rows; ++i) s2 += A[(size_t)i * cols + j] * A[(size_t)i * cols + j];
+      cn[j] = s2;
+    }
+  }
+  return r;
+}
+
+// For every edge (child node c): the terms split into the operator string on the subtree of c
+// and the string on the rest of the tree; the coefficient matrix C[subtree string][rest string]
+// (sum of the coefficients of the terms with those two parts) has the smallest bond any exact
+// TTNO of H can have on that edge as its rank, when distinct strings are linearly independent
+// operators. The rank is taken by pivoted QR with a relative tolerance of 1e-12.
+static std::vector<int> edge_rank_bounds(const TreeInfo& tree, int n_terms, const double* coeff,
+                                         const int* term_offset, const int* term_op_ids,
+                                         const int* op_site) {
+  std::vector<int> out(tree.n, 1);
+  for (int c = 0; c < tree.n; ++c) {
+    if (c == tree.root) continue;
+    std::vector<char> in_sub(tree.n, 0);
+    std::vector<int> st{c};
+    while (!st.empty()) {
+      const int u = st.back();
+      st.pop_back();
+      in_sub[u] = 1;
+      for (int ch : tree.children[u]) st.push_back(ch);
+    }
+    std::map<std::vector<int>, int> L, R;
+    std::vector<std::tuple<int, int, double>> nz;
+    for (int t = 0; t < n_terms; ++t) {
+      if (coeff[t] == 0.0) continue;
+      std::vector<int> l, r;
+      for (int k = term_offset[t]; k < term_offset[t + 1]; ++k)
+        (in_sub[op_site[term_op_ids[k]]] ? l : r).push_back(term_op_ids[k]);
+      std::sort(l.begin(), l.end());
+      std::sort(r.begin(), r.end());
+      const int li = L.emplace(l, (int)L.size()).first->second;
+      const int ri = R.emplace(r, (int)R.size()).first->second;
+      nz.emplace_back(li, ri, coeff[t]);
+    }
+    const int rows = (int)L.size(), cols = (int)R.size();
+    if (rows == 0 || cols == 0) {
+      out[c] = 0;
+      continue;
+    }
+    std::vector<double> A((size_t)rows * cols, 0.0);
+    for (auto& e : nz) A[(size_t)std::get<0>(e) * cols + std::get<1>(e)] += std::get<2>(e);
+    out[c] = pivoted_qr_rank(A, rows, cols, 1e-12);
+  }
+  return out;
 }
 
 static ttn_ttno* build_ttno_impl(ttn_ctx* ctx, const TreeInfo& tree, int n_ops,
@@ -606,6 +698,7 @@ ttn_status ttn_create(ttn_ctx** out, int device, void* cuda_stream) {
     void* dw = nullptr;
     CUDA_CHECK(cudaHostGetDevicePointer(&dw, hw, 0));
     ctx->d_wait = static_cast<unsigned*>(dw);
+    if (const char* lp = getenv("TTN_LAUNCH_LOG")) ctx->launch_log = std::fopen(lp, "a");
     cudaMemPool_t pool;
     CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, device));
     uint64_t thr = UINT64_MAX;
@@ -636,6 +729,7 @@ void ttn_destroy(ttn_ctx* ctx) {
   for (auto e : ctx->iter_ev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->h_wait) cudaFreeHost(ctx->h_wait);
+  if (ctx->launch_log) std::fclose(ctx->launch_log);
   delete ctx;
 }
 
@@ -744,6 +838,8 @@ ttn_status ttn_build_ttno(ttn_ctx* ctx, const ttn_tree* tree, int n_ops, const i
     TTN_REQUIRE(tol >= 0.0, "tol must be >= 0");
     ttn_ttno* H = build_ttno_impl(ctx, tree->info, n_ops, op_site, op_offset, op_data, n_terms,
                                   coeff, term_offset, term_op_ids, tol);
+    H->rank_bound = edge_rank_bounds(tree->info, n_terms, coeff, term_offset, term_op_ids,
+                                     op_site);
     if (bond_dims_out)
       for (int i = 0; i < tree->info.n; ++i) bond_dims_out[i] = H->wbond[i];
     *out = H;
@@ -786,6 +882,13 @@ ttn_status ttn_ttno_create(ttn_ctx* ctx, const ttn_tree* tree, const int* wbond,
     }
     *out = H.release();
   });
+}
+
+ttn_status ttn_ttno_rank_bounds(const ttn_ttno* H, int* rank_out) {
+  if (!H || !rank_out) return TTN_EINVAL;
+  for (int i = 0; i < H->tree.n; ++i)
+    rank_out[i] = i < (int)H->rank_bound.size() ? H->rank_bound[i] : -1;
+  return TTN_OK;
 }
 
 ttn_status ttn_ttno_info(const ttn_ttno* H, int* wbond_out, int* n_entries_out,
@@ -895,14 +998,13 @@ ttn_status ttn_block_copy_states(ttn_block* dst, const ttn_block* src, int n,
     TTN_REQUIRE(dst->tree.same_shape(src->tree) && dst->bond == src->bond,
                 "copy_states: blocks differ in tree or bonds");
     TTN_REQUIRE(n <= dst->n_states, "copy_states: too many states");
-    for (int j = 0; j < n; ++j) {
+    for (int j = 0; j < n; ++j)
       TTN_REQUIRE(src_states[j] >= 0 && src_states[j] < src->n_states, "bad source state");
-      for (int t = 0; t < dst->tree.n; ++t)
-        CUDA_CHECK(cudaMemcpyAsync(dst->node64(t) + (long long)j * dst->size[t],
-                                   src->node64(t) + (long long)src_states[j] * src->size[t],
-                                   dst->size[t] * sizeof(double), cudaMemcpyDeviceToDevice,
-                                   dst->ctx->stream));
-    }
+    if (n == 0) return;
+    TTN_REQUIRE(dst != src, "copy_states: source and destination are the same block");
+    DevInts idx(std::vector<int>(src_states, src_states + n), dst->ctx->stream);
+    for (int t = 0; t < dst->tree.n; ++t)     // one gather launch per node
+      launch_gather_rows(dst->ctx, dst->node64(t), src->node64(t), idx.get(), n, dst->size[t]);
     dst->touch();
   });
 }

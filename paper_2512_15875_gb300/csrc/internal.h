@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <map>
 #include <memory>
 #include <string>
@@ -113,6 +114,10 @@ struct ttn_ctx {
   // and one after each iteration (index 0: the initial Rayleigh quotients), on the stream.
   std::vector<cudaEvent_t> iter_ev;
   int iter_marks = 0;
+  // Per-launch log (kernel name, algorithmic flops and bytes, one line per launch issued outside
+  // graph capture), opened when the environment variable TTN_LAUNCH_LOG names a file; lets a
+  // counter capture of single launches be matched with the work those launches did.
+  FILE* launch_log = nullptr;
 };
 
 // Records the iteration clock's start (mark 0 .. ) on the context stream.
@@ -226,6 +231,9 @@ struct ttn_ttno {
   std::vector<long long> op_off;
   std::vector<double> op_data;
   std::vector<std::vector<TtnoEntry>> entries;
+  // Per edge (child node): numerical rank of the sum-of-products coefficient matrix across the
+  // edge, the smallest bond of any exact TTNO of H there (-1 where unknown, 1 at the root).
+  std::vector<int> rank_bound;
   std::map<long long, NodePlan> plans;
   std::map<std::vector<long long>, DevTables> tables;
   int wdim(int node, int leg) const {
@@ -326,6 +334,18 @@ bool level_shape_ok(const GemmDesc& g);
 // (0 when that kernel does not take the shape).
 int level_group_cap(int M, int N, int K);
 template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
+// Closure of an auxiliary node's environment update fused into its segmented level stage.
+struct SegClose {
+  const float* bra;        // permuted bra tensors [state][a_open][grp * N]
+  long long bra_pstride;   // floats per bra state
+  int da, db;              // a_open and b_open values
+  int grp;                 // rows of Z per b_open value (Z rows are (b_open, rest))
+  float* out;              // environments [pair][slot][a_open][b_open]
+  long long out_pstride;   // floats per pair
+};
+bool seg_close_ok(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c);
+void launch_level_seg_close(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c, long long out_len,
+                            long long bra_len);
 // Tensor-core (TF32 MMA, 3xTF32 split) level stage for float data, N <= 32, K <= 64.
 bool level_tc_ok(const GemmDesc& g);
 void launch_level_tc(ttn_ctx* ctx, const GemmDesc& g);
@@ -368,6 +388,9 @@ void launch_to_f32(ttn_ctx* ctx, const double* in, float* out, long long n);
 void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n);
 void launch_scatter_gram(ttn_ctx* ctx, const double* g, int n_pairs, const int* pb,
                          const int* pk, int symmetric, double* out, int ld);
+// dst[j][:] = src[d_idx[j]][:] for j < n_rows (rows of `size` doubles; d_idx on the device).
+void launch_gather_rows(ttn_ctx* ctx, double* dst, const double* src, const int* d_idx,
+                        int n_rows, long long size);
 // Counts the non-finite entries of rows x cols (leading dimension ld) into *d_count (device).
 void launch_count_nonfinite(ttn_ctx* ctx, const double* a, int rows, int cols, int ld,
                             unsigned* d_count);

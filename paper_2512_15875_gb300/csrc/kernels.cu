@@ -215,6 +215,16 @@ __global__ void count_nonfinite_kernel(const double* __restrict__ a, int rows, i
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
 }
 
+// dst[j][r] = src[idx[j]][r] for j < n_rows, r < size (rows of `size` doubles)
+__global__ void gather_rows_kernel(double* __restrict__ dst, const double* __restrict__ src,
+                                   const int* __restrict__ idx, long long size, long long total) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / size;
+    dst[i] = src[(long long)idx[j] * size + (i - j * size)];
+  }
+}
+
 int grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
   if (b > 152 * 32) b = 152 * 32;
@@ -257,7 +267,7 @@ static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
 
 // Host-side proof that every address the launch can form lies inside its buffer: for each item
 // and segment, the smallest and largest offsets over (m, n, k) and over all pairs.
-static void check_bounds(const GemmDesc& g, size_t elem) {
+static void check_bounds(const GemmDesc& g, size_t elem, bool check_c = true) {
   auto base_max = [&](int mode, long long pstride) -> long long {
     if (mode == MODE_PAIR) return (long long)(g.n_pairs - 1) * pstride;
     if (mode == MODE_BRA) return (long long)g.max_bra * pstride;
@@ -273,7 +283,7 @@ static void check_bounds(const GemmDesc& g, size_t elem) {
                          (long long)(g.N - 1) * g.c_sn;
   for (int s = 0; s < g.st.n_sub; ++s) {
     const long long c0 = g.hst->sub_c[s];
-    if (c0 < 0 || c0 + c_hi >= g.c_len)
+    if (check_c && (c0 < 0 || c0 + c_hi >= g.c_len))
       TTN_FAIL(TTN_EINVAL, "gemm bounds: C item %d reaches %lld of %lld (elem %zu)", s, c0 + c_hi,
                g.c_len, elem);
     if (g.K <= 0) continue;
@@ -303,6 +313,8 @@ static cudaEvent_t pool_event(ttn_ctx* ctx) {
 LaunchScope::LaunchScope(ttn_ctx* c, const char* name, double flops, double bytes) : ctx(c) {
   ctx->launches++;
   ctx->flops_total += flops;
+  if (ctx->launch_log && !ctx->capturing)
+    std::fprintf(ctx->launch_log, "%s\t%.17g\t%.17g\n", name, flops, bytes);
   if (!ctx->profiling || ctx->capturing) return;
   int id = -1;
   for (size_t i = 0; i < ctx->prof_names.size(); ++i)
@@ -431,6 +443,15 @@ void launch_to_f64(ttn_ctx* ctx, const float* in, double* out, long long n) {
   if (n == 0) return;
   LaunchScope ls(ctx, "to_f64", 0.0, 12.0 * n);
   to_f64_kernel<<<grid_for(n), kThreads, 0, ctx->stream>>>(in, out, n);
+  CUDA_LAUNCH_CHECK();
+}
+
+void launch_gather_rows(ttn_ctx* ctx, double* dst, const double* src, const int* d_idx,
+                        int n_rows, long long size) {
+  const long long total = (long long)n_rows * size;
+  if (total == 0) return;
+  LaunchScope ls(ctx, "gather_states", 0.0, 16.0 * total);
+  gather_rows_kernel<<<grid_for(total), kThreads, 0, ctx->stream>>>(dst, src, d_idx, size, total);
   CUDA_LAUNCH_CHECK();
 }
 
@@ -1181,6 +1202,136 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
                          nrow, g.N, acc, vec_store);
 }
 
+// Named barrier over the compute warps only (the producer warp has left by then).
+__device__ __forceinline__ void compute_warps_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Segmented level stage of an auxiliary node fused with the closure of its environment
+// update: the warp-specialised segment loop of level_seg_ws_kernel produces this CTA's row tile
+// of Z[slot] (rows (b_open, a_rest), columns a_last) in registers; the tile, whose rows cover
+// whole b_open values (c.grp rows each), goes to shared memory and is closed at once with the
+// bra, E[slot][a_open][b_open] = sum_k bra[a_open][k] Z[b_open][k] (k = (a_rest, a_last)), the
+// bra streamed through shared memory in chunks of kSegCloseKC. Z never reaches global memory.
+// A compute warp whose bounded wait gave up stops computing but still reaches the compute-warp
+// barrier, so every warp leaves together.
+constexpr int kSegCloseKC = 96;
+constexpr int kSegCloseMaxOut = 4;
+template <int NA>
+__global__ void __launch_bounds__(320) level_seg_close_kernel(GemmDesc g, SegClose c, int rtiles,
+                                                              int rows_cta) {
+  extern __shared__ __align__(16) float dsm[];
+  __shared__ __align__(8) unsigned long long full[2];
+  __shared__ __align__(8) unsigned long long empty[2];
+  __shared__ int failed;
+  const int nw = rows_cta >> 5;
+  const int stage = g.K * rows_cta + g.K * NA;
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int sub = (int)(rest % g.st.n_sub);
+  const int pair = (int)(rest / g.st.n_sub);
+  const int s0 = g.st.seg_ptr[sub], nseg = g.st.seg_ptr[sub + 1] - s0;
+  const int r0 = rt * rows_cta;
+  const int nrow = min(rows_cta, g.M - r0);
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], nw);
+    mbar_init(&empty[1], nw);
+    mbar_init_fence();
+    failed = 0;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == nw) {
+    if (lane == 0) {
+      const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+      const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+      for (int j = 0; j < nseg; ++j) {
+        const int st = j & 1;
+        if (j >= 2 && !mbar_wait(&empty[st], ((j >> 1) - 1) & 1, g.wait_flag)) break;
+        fence_proxy_async();
+        float* As = dsm + st * stage;
+        float* Es = As + g.K * rows_cta;
+        const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
+        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
+        for (int b = 0; b < g.K; ++b)
+          bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
+        bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
+      }
+    }
+    return;
+  }
+  const int nthreads = nw * 32;
+  const bool live = warp * 32 < nrow;   // warp-uniform
+  float acc[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+  bool ok = true;
+  for (int j = 0; j < nseg && ok; ++j) {
+    const int st = j & 1;
+    ok = mbar_wait(&full[st], (j >> 1) & 1, g.wait_flag);
+    if (!ok) break;
+    const float* As = dsm + st * stage;
+    if (live) level_mac<NA, false>(As, rows_cta, As + g.K * rows_cta, g.K, acc);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  if (!ok && lane == 0) atomicOr(&failed, 1);
+  compute_warps_sync(nthreads);          // every copy has landed and every warp is done
+  if (failed) return;
+  // this warp's rows of the Z tile -> shared memory, row stride N (= NA)
+  float* Zs = dsm;
+  if (live) {
+    constexpr int CPT = NA / 4;
+    const int rl = warp * 32 + (lane >> 2) * 4, cg = lane & 3;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (rl + i < nrow) {
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) Zs[(rl + i) * NA + cg * CPT + cc] = acc[i * CPT + cc];
+      }
+  }
+  float* Bs = dsm + stage;               // bra chunk [a_open][kSegCloseKC + 1]
+  const int K2 = c.grp * NA;             // closure contraction length
+  const int nb0 = nrow / c.grp;          // b_open values of this tile
+  const int nout = c.da * nb0;
+  const float* bra = c.bra + (long long)g.pair_bra[pair] * c.bra_pstride;
+  float cacc[kSegCloseMaxOut];
+#pragma unroll
+  for (int q = 0; q < kSegCloseMaxOut; ++q) cacc[q] = 0.f;
+  for (int k0 = 0; k0 < K2; k0 += kSegCloseKC) {
+    const int kc = min(kSegCloseKC, K2 - k0);
+    compute_warps_sync(nthreads);        // Zs written / previous chunk consumed
+    for (int i = threadIdx.x; i < c.da * kc; i += nthreads) {
+      const int a = i / kc, k = i - a * kc;
+      Bs[a * (kSegCloseKC + 1) + k] = bra[(long long)a * K2 + k0 + k];
+    }
+    compute_warps_sync(nthreads);
+#pragma unroll
+    for (int q = 0; q < kSegCloseMaxOut; ++q) {
+      const int o = threadIdx.x + q * nthreads;
+      if (o >= nout) break;
+      const int a = o % c.da, b0l = o / c.da;
+      const float* zr = Zs + b0l * K2 + k0;
+      const float* br = Bs + a * (kSegCloseKC + 1);
+      float s = 0.f;
+      for (int k = 0; k < kc; ++k) s = fmaf(br[k], zr[k], s);
+      cacc[q] += s;
+    }
+  }
+  const int b00 = r0 / c.grp;
+  float* out = c.out + (long long)pair * c.out_pstride + (long long)sub * c.da * c.db;
+#pragma unroll
+  for (int q = 0; q < kSegCloseMaxOut; ++q) {
+    const int o = threadIdx.x + q * nthreads;
+    if (o >= nout) break;
+    const int a = o % c.da, b0l = o / c.da;
+    out[(long long)a * c.db + b00 + b0l] = cacc[q];
+  }
+}
+
 namespace {
 int level_tma_na(int N) { return N <= 8 ? 8 : N <= 16 ? 16 : N <= 24 ? 24 : N <= 32 ? 32 : 0; }
 int level_tma_rows(int M) {
@@ -1227,6 +1378,73 @@ static bool level_tma_ok(const GemmDesc& g) {
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
     return false;
   return g.hst->a4 && g.hst->b4;
+}
+
+// Rows per CTA of the fused segmented-level + closure kernel: whole warps, whole b_open groups
+// of grp rows, at most 9 compute warps, balanced over the row tiles; 0 if none fits.
+static int seg_close_rows(int M, int grp) {
+  if (grp <= 0 || M % grp != 0) return 0;
+  int best = 0;
+  for (int r = 32; r <= 288; r += 32)
+    if (r % grp == 0) best = r;
+  if (best == 0) return 0;
+  const int tiles = (M + best - 1) / best;
+  const int per = (M / grp + tiles - 1) / tiles * grp;      // b_open groups split evenly
+  for (int r = 32; r <= best; r += 32)
+    if (r % grp == 0 && r >= per) return r;
+  return best;
+}
+
+bool seg_close_ok(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c) {
+  if (ctx->tf32x3 || !level_tma_ok(g) || g.st.n_grp != 0) return false;
+  const int na = level_tma_na(g.N);
+  if (na != g.N || !(g.b_sn == 1 && g.b_sk == g.N && g.K != 1)) return false;
+  const int rows = seg_close_rows(g.M, c.grp);
+  if (rows == 0 || c.grp * c.db != g.M) return false;
+  if ((long long)c.da * (rows / c.grp) > (long long)kSegCloseMaxOut * rows) return false;
+  const size_t stage = (size_t)g.K * rows + (size_t)g.K * na;
+  if ((size_t)rows * na > stage || (size_t)c.da * (kSegCloseKC + 1) > stage) return false;
+  return sizeof(float) * 2 * stage <= kLevelTmaSmem;
+}
+
+void launch_level_seg_close(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c, long long out_len,
+                            long long bra_len) {
+  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
+  TTN_REQUIRE(seg_close_ok(ctx, g, c), "fused level + closure: unsupported shape");
+  check_bounds(g, sizeof(float), false);     // A and B; the output is checked below
+  const long long K2 = (long long)c.grp * g.N;
+  TTN_REQUIRE((long long)(g.n_pairs - 1) * c.out_pstride + (long long)g.st.n_sub * c.da * c.db <=
+                  out_len,
+              "fused closure bounds: output");
+  TTN_REQUIRE((long long)g.max_bra * c.bra_pstride + c.da * K2 <= bra_len,
+              "fused closure bounds: bra");
+  const int na = level_tma_na(g.N);
+  const int rows_cta = seg_close_rows(g.M, c.grp);
+  const int rt = (g.M + rows_cta - 1) / rows_cta;
+  const long long grid = (long long)rt * g.st.n_sub * g.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+  const double flops = 2.0 * g.M * g.N * (double)g.K * g.hst->n_seg * g.n_pairs +
+                       2.0 * c.da * c.db * (double)K2 * g.st.n_sub * g.n_pairs;
+  const double bytes = algorithmic_bytes(g, sizeof(float)) +
+                       4.0 * std::min(g.n_pairs, g.max_bra + 1) * c.da * K2 +
+                       4.0 * g.n_pairs * g.st.n_sub * c.da * c.db;
+  static const char* nm[] = {"level_seg_close_f32_8", "level_seg_close_f32_16",
+                             "level_seg_close_f32_24", "level_seg_close_f32_32"};
+  LaunchScope ls(ctx, nm[na / 8 - 1], flops, bytes);
+  GemmDesc gd = g;
+  gd.wait_flag = ctx->d_wait;
+  const size_t smem = sizeof(float) * 2 * ((size_t)g.K * rows_cta + (size_t)g.K * na);
+  auto go = [&](auto kern) {
+    smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
+    kern<<<(unsigned)grid, rows_cta + 32, smem, ctx->stream>>>(gd, c, rt, rows_cta);
+  };
+  switch (na) {
+    case 8: go(level_seg_close_kernel<8>); break;
+    case 16: go(level_seg_close_kernel<16>); break;
+    case 24: go(level_seg_close_kernel<24>); break;
+    default: go(level_seg_close_kernel<32>); break;
+  }
+  CUDA_LAUNCH_CHECK();
 }
 
 template <class T>

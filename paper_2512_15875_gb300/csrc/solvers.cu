@@ -1360,22 +1360,16 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
     const int m = have_p ? 3 * n : 2 * n;
     auto S = new_block(m);
     {
-      std::vector<int> ids(n);
-      std::iota(ids.begin(), ids.end(), 0);
-      // gather into S by copying the three blocks' states
-      for (int j = 0; j < n; ++j) {
-        for (int t = 0; t < tr.n; ++t) {
-          const long long sz = x->size[t];
-          CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)j * sz, x->node64(t) + (long long)j * sz,
-                                     sz * sizeof(double), cudaMemcpyDeviceToDevice, st));
-          CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)(n + j) * sz,
-                                     Y->node64(t) + (long long)j * sz, sz * sizeof(double),
+      // S = x, y, p in that order: each node's three slabs are contiguous copies
+      for (int t = 0; t < tr.n; ++t) {
+        const size_t bytes = (size_t)n * x->size[t] * sizeof(double);
+        double* dst = S->node64(t);
+        CUDA_CHECK(cudaMemcpyAsync(dst, x->node64(t), bytes, cudaMemcpyDeviceToDevice, st));
+        CUDA_CHECK(cudaMemcpyAsync(dst + (long long)n * x->size[t], Y->node64(t), bytes,
+                                   cudaMemcpyDeviceToDevice, st));
+        if (have_p)
+          CUDA_CHECK(cudaMemcpyAsync(dst + 2LL * n * x->size[t], P->node64(t), bytes,
                                      cudaMemcpyDeviceToDevice, st));
-          if (have_p)
-            CUDA_CHECK(cudaMemcpyAsync(S->node64(t) + (long long)(2 * n + j) * sz,
-                                       P->node64(t) + (long long)j * sz, sz * sizeof(double),
-                                       cudaMemcpyDeviceToDevice, st));
-        }
       }
       S->touch();
     }
@@ -1404,39 +1398,44 @@ static void lobpcg_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int n_iter, dou
                                st));
     CUDA_CHECK(cudaStreamSynchronize(st));
     // x_j = sum_k v_kj s_k (normalised), p_j = sum_{k >= n} v_kj s_k
-    auto fit_comb = [&](ttn_block* out, int k0) {
-      std::vector<int> init(n);
+    // x_j and p_j are fitted in one batch of 2n output states (outputs 0..n-1: x_j from all of
+    // S; outputs n..2n-1: p_j from the states k >= n); every output's fit is independent.
+    {
+      PhaseScope ph(ctx, "fit_xp");
+      auto XP = new_block(2 * n);
+      std::vector<int> init(2 * n);
       FitGroup g{Id, S.get(), {}, {}, {}};
-      for (int j = 0; j < n; ++j) {
-        int arg = k0;
-        double best = -1.0;
-        for (int k = k0; k < m; ++k) {
-          const double c = hV[(size_t)k * n + j];
-          if (std::fabs(c) > best) {
-            best = std::fabs(c);
-            arg = k;
+      for (int half = 0; half < 2; ++half) {
+        const int k0 = half * n;
+        for (int j = 0; j < n; ++j) {
+          int arg = k0;
+          double best = -1.0;
+          for (int k = k0; k < m; ++k) {
+            const double c = hV[(size_t)k * n + j];
+            if (std::fabs(c) > best) {
+              best = std::fabs(c);
+              arg = k;
+            }
+            if (c != 0.0) {
+              g.out_j.push_back(half * n + j);
+              g.in_k.push_back(k);
+              g.coef.push_back(c);
+            }
           }
-          if (c != 0.0) {
-            g.out_j.push_back(j);
-            g.in_k.push_back(k);
-            g.coef.push_back(c);
-          }
+          init[half * n + j] = arg;
         }
-        init[j] = arg;
       }
-      ttn_status cs = ttn_block_copy_states(out, S.get(), n, init.data());
+      ttn_status cs = ttn_block_copy_states(XP.get(), S.get(), 2 * n, init.data());
       if (cs != TTN_OK) TTN_FAIL(cs, "copy");
       std::vector<FitGroup> gs{g};
-      fit_impl<T>(ctx, gs, out, fit_sweeps);
-    };
-    {
-      PhaseScope ph(ctx, "fit_x");
-      fit_comb(Xn.get(), 0);
+      fit_impl<T>(ctx, gs, XP.get(), fit_sweeps);
+      std::vector<int> lo(n), hi(n);
+      std::iota(lo.begin(), lo.end(), 0);
+      std::iota(hi.begin(), hi.end(), n);
+      cs = ttn_block_copy_states(Xn.get(), XP.get(), n, lo.data());
+      if (cs == TTN_OK) cs = ttn_block_copy_states(Pn.get(), XP.get(), n, hi.data());
+      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
       normalize_states<T>(ctx, Xn.get(), prec);
-    }
-    {
-      PhaseScope ph(ctx, "fit_p");
-      fit_comb(Pn.get(), n);
     }
     std::swap(P, Pn);
     have_p = true;

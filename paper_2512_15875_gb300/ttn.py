@@ -71,6 +71,7 @@ _SIGS = {
     "ttn_src_apply": (_I, [_P, _P, _P, _I, _DP, C.POINTER(_P), _I]),
     "ttn_selftest_bounded_wait": (_I, [_P, _D]),
     "ttn_iteration_times": (_I, [_P, _DP, _I]),
+    "ttn_ttno_rank_bounds": (_I, [_P, _IP]),
     "ttn_fault_inject_alloc": (None, [_LL]),
 }
 
@@ -276,6 +277,14 @@ def ttn_build_ttno(ctx, tree_h, flat, tol=1e-12):
         _ip(f["term_offset"].astype(np.int32)), _ip(f["term_op_ids"].astype(np.int32)),
         float(tol), C.byref(p), _ip(bonds)))
     return TTNO(p.value, ctx), bonds
+
+
+def ttn_ttno_rank_bounds(H, n_nodes):
+    """Per edge: the smallest operator bond an exact TTNO can have (numerical rank of the
+    coefficient matrix across the edge); -1 where unknown."""
+    out = np.zeros(n_nodes, dtype=np.int32)
+    H.ctx.check(load().ttn_ttno_rank_bounds(H.ptr, _ip(out)))
+    return out
 
 
 def ttn_ttno_create(ctx, tree_h, wbond, ops, entries):

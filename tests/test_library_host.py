@@ -126,3 +126,65 @@ def test_host_only_context_refuses_device_blocks(ttn, hctx):
     th = ttn.ttn_tree_create(hctx, tree)
     with pytest.raises(ttn.TTNError):
         ttn.ttn_block_create(hctx, th, 2, I.uniform_bonds(tree, 2))
+
+
+def _operator_schmidt_rank(H, dims, sub_modes):
+    """Rank of the dense operator realigned as (operators on the subtree's modes) x (operators
+    on the other modes): the smallest bond of any exact TTNO across that edge."""
+    L = len(dims)
+    T = H.reshape(list(dims) + list(dims))
+    rest = [m for m in range(L) if m not in sub_modes]
+    order = list(sub_modes) + [L + m for m in sub_modes] + rest + [L + m for m in rest]
+    rows = int(np.prod([dims[m] ** 2 for m in sub_modes]))
+    M = np.transpose(T, order).reshape(rows, -1)
+    s = np.linalg.svd(M, compute_uv=False)
+    return int(np.sum(s > 1e-10 * s[0]))
+
+
+@pytest.mark.parametrize("name,mk", TREES[:4])
+def test_rank_bound_is_the_operator_schmidt_rank(ttn, hctx, name, mk):
+    tree = mk(3)
+    rng = np.random.default_rng(11)
+    L = int(tree.mode.max()) + 1
+    ham = I.Hamiltonian(dims=[3] * L, omega=rng.uniform(1.0, 2.0, L))
+    for i in range(L):
+        ham.add(ham.omega[i], {i: "h"})
+    for i in range(L):
+        for j in range(i + 1, L):
+            ham.add_monomial(rng.normal(0, 0.3), (i, j))
+    for _ in range(L):
+        ham.add_monomial(rng.normal(0, 0.1), tuple(sorted(rng.integers(0, L, 3))))
+    th = ttn.ttn_tree_create(hctx, tree)
+    H, bonds = ttn.ttn_build_ttno(hctx, th, ham.flat(tree))
+    rk = ttn.ttn_ttno_rank_bounds(H, tree.n_nodes)
+    Hd = N.dense_hamiltonian(ham)
+    for c in range(tree.n_nodes):
+        if tree.parent[c] < 0:
+            continue
+        sub = sorted(int(tree.mode[u]) for u in tree.subtree(c) if tree.mode[u] >= 0)
+        assert rk[c] == _operator_schmidt_rank(Hd, ham.dims, sub), c
+        assert bonds[c] >= rk[c]
+
+
+def test_rank_bound_of_the_uniform_bilinear_model_is_three(ttn, hctx):
+    # Sec. III.A: the uniformly coupled model has an exact TTNO of bond 3 on every MPS edge, and
+    # no exact TTNO with a smaller bond exists
+    ham = I.uniform_coupled_model(n_modes=16, d=4)
+    tree = I.mps_tree(16, 4)
+    th = ttn.ttn_tree_create(hctx, tree)
+    H, bonds = ttn.ttn_build_ttno(hctx, th, ham.flat(tree))
+    rk = ttn.ttn_ttno_rank_bounds(H, tree.n_nodes)
+    assert list(rk[1:]) == [3] * 15 and list(bonds[1:]) == [3] * 15
+
+
+@pytest.mark.parametrize("name", ["c2", "c3", "c4", "c5"])
+def test_built_bond_reaches_the_rank_bound_on_the_workloads(ttn, hctx, name):
+    # the merged state diagram with a minimum vertex cover per edge is optimal on these
+    # Hamiltonians: every edge's bond equals the smallest bond an exact TTNO can have
+    w = I.make_workload(name)
+    th = ttn.ttn_tree_create(hctx, w.tree)
+    H, bonds = ttn.ttn_build_ttno(hctx, th, w.ham.flat(w.tree))
+    rk = ttn.ttn_ttno_rank_bounds(H, w.tree.n_nodes)
+    for c in range(w.tree.n_nodes):
+        if w.tree.parent[c] >= 0:
+            assert 1 <= rk[c] == bonds[c], (c, rk[c], bonds[c])
