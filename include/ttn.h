@@ -282,6 +282,18 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
                                  double minres_tol, int fit_sweeps, ttn_precision prec,
                                  double* rq_hist);
 
+/* ---- generalized eigenvalue problem over a block (Sec. III.B, Alg. 3 orthogonalisation) ---- */
+
+/* Hc = ESc over all states of x: the Gram matrices <x_k|H|x_l> and <x_k|x_l> are formed, the
+ * pencil is solved by canonical orthogonalisation (overlap eigenvalues below eps * max
+ * dropped), and each state is replaced by its Ritz vector sum_l c_la x_l, fitted back into x's
+ * bonds (fit_sweeps sweeps) and normalised. theta[n_states] (may be NULL) receives the Ritz
+ * values in ascending order. This removes the residual non-orthogonality between states that
+ * block inverse iteration leaves across its blocks. Returns TTN_EINVAL if fewer than n_states
+ * directions survive eps. */
+ttn_status ttn_block_rayleigh_ritz(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, double eps,
+                                   int fit_sweeps, ttn_precision prec, double* theta);
+
 /* ---- Rayleigh-Ritz without device allocation --------------------------------------------- */
 
 /* The paper has no counterpart to this call. It serves callers that may not allocate device

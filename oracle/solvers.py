@@ -312,3 +312,18 @@ def inverse_iteration(tree, ttno, X0, n_iter, clusters, als_sweeps=1, minres_max
         X, lam = Xn, lam_n
         hist.append(lam.copy())
     return lam, X, hist
+
+
+def block_rayleigh_ritz(tree, ttno, X, fit_sweeps=2, eps=1e-12):
+    """The generalized eigenvalue problem Hc = ESc over all states (Sec. III.B): Gram matrices
+    over X, canonical orthogonalisation, each state replaced by its fitted and normalised Ritz
+    vector (fitting starts from the input state of the largest |coefficient|).
+    Returns (Ritz values, states)."""
+    idt = identity_ttno(tree)
+    Ht, Mt = gram_block(tree, ttno, X)
+    theta, V = rayleigh_ritz(Ht, Mt, len(X), eps)
+    out = []
+    for a in range(len(X)):
+        tx = [(V[b, a], idt, X[b]) for b in range(len(X))]
+        out.append(normalize(tree, fit(tree, tx, fit_initial(tx), fit_sweeps)))
+    return theta, out

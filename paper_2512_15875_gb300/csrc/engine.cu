@@ -397,31 +397,13 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
 
   const long long zsize = sizes[mC];
   const long long zrest = zsize / d;
-  // auxiliary node, environment output, float32 SIMT: the closure runs inside the segmented
-  // level stage and Z is never stored (decided on the level stage's descriptor below)
-  bool fuse_close = false;
-  DevBuf bperm;
-  auto permute_bra = [&]() {
-    std::vector<int> bd(Da.begin(), Da.end());
-    bd.push_back(d);
-    std::vector<int> bp_order = {open};
-    bp_order.insert(bp_order.end(), p.C.begin(), p.C.end());
-    bp_order.push_back(nl);
-    const long long bsize = bra->size[t];
-    bperm = DevBuf((size_t)bra->n_states * bsize * sizeof(T), st);
-    launch_permute<T>(ctx, block_node<T>(bra, t), bperm.as<T>(), bra->n_states, nl + 1, bd.data(),
-                      bp_order.data());
-  };
   DevBuf zbuf;
   void* Z = out;
+  if (out_kind != OUT_LOCAL) {
+    zbuf = DevBuf((size_t)P * p.n_slots * zsize * sizeof(T), st);
+    Z = zbuf.p;
+  }
   const long long z_len = out_kind == OUT_LOCAL ? out_len : (long long)P * p.n_slots * zsize;
-  auto alloc_z = [&]() {
-    if (out_kind != OUT_LOCAL) {
-      zbuf = DevBuf((size_t)P * p.n_slots * zsize * sizeof(T), st);
-      Z = zbuf.p;
-    }
-  };
-  if (!p.fused) alloc_z();
   if (p.fused) {
     // fold the TTNO into the last contracted leg's environment, then one segmented level stage
     const int c = p.C[mC - 1];
@@ -463,28 +445,8 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     g.alg_a = prev_mode == MODE_KET;
     g.alg_b = false;           // folded environments (their sources count in combine_env)
     g.alg_c = out_kind == OUT_LOCAL;
-    SegClose sc{};
-    if (sizeof(T) == 4 && out_kind == OUT_ENV && level_shape_ok(g)) {
-      sc.bra_pstride = bra->size[t];
-      sc.da = Da[open];
-      sc.db = Db[open];
-      sc.grp = (int)(rest / Db[open]);
-      sc.out = static_cast<float*>(out);
-      sc.out_pstride = (long long)p.n_slots * Da[open] * Db[open];
-      fuse_close = rest % Db[open] == 0 && seg_close_ok(ctx, g, sc);
-    }
-    if (fuse_close) {
-      permute_bra();
-      sc.bra = bperm.as<float>();
-      g.C = nullptr;
-      g.c_len = 0;
-      launch_level_seg_close(ctx, g, sc, out_len, (long long)bra->n_states * bra->size[t]);
-    } else {
-      alloc_z();
-      g.C = Z;
-      if (level_shape_ok(g)) launch_level<T>(ctx, g);
-      else launch_gemm<T>(ctx, g);
-    }
+    if (level_shape_ok(g)) launch_level<T>(ctx, g);
+    else launch_gemm<T>(ctx, g);
   } else {
     OpStageDesc o{};
     o.d = d;
@@ -512,10 +474,16 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
     launch_op_stage<T>(ctx, o);
   }
 
-  if (out_kind == OUT_ENV && !fuse_close) {
-    permute_bra();
+  if (out_kind == OUT_ENV) {
+    std::vector<int> bd(Da.begin(), Da.end());
+    bd.push_back(d);
+    std::vector<int> bperm = {open};
+    bperm.insert(bperm.end(), p.C.begin(), p.C.end());
+    bperm.push_back(nl);
     const long long bsize = bra->size[t];
-    DevBuf& bp = bperm;
+    DevBuf bp((size_t)bra->n_states * bsize * sizeof(T), st);
+    launch_permute<T>(ctx, block_node<T>(bra, t), bp.as<T>(), bra->n_states, nl + 1, bd.data(),
+                      bperm.data());
     const long long K = zsize / Db[open];
     GemmDesc g{};
     g.M = Da[open];

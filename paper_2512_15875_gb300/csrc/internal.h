@@ -334,18 +334,6 @@ bool level_shape_ok(const GemmDesc& g);
 // (0 when that kernel does not take the shape).
 int level_group_cap(int M, int N, int K);
 template <class T> void launch_level(ttn_ctx* ctx, const GemmDesc& g);
-// Closure of an auxiliary node's environment update fused into its segmented level stage.
-struct SegClose {
-  const float* bra;        // permuted bra tensors [state][a_open][grp * N]
-  long long bra_pstride;   // floats per bra state
-  int da, db;              // a_open and b_open values
-  int grp;                 // rows of Z per b_open value (Z rows are (b_open, rest))
-  float* out;              // environments [pair][slot][a_open][b_open]
-  long long out_pstride;   // floats per pair
-};
-bool seg_close_ok(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c);
-void launch_level_seg_close(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c, long long out_len,
-                            long long bra_len);
 // Tensor-core (TF32 MMA, 3xTF32 split) level stage for float data, N <= 32, K <= 64.
 bool level_tc_ok(const GemmDesc& g);
 void launch_level_tc(ttn_ctx* ctx, const GemmDesc& g);

@@ -267,7 +267,7 @@ static double algorithmic_bytes(const GemmDesc& g, size_t elem) {
 
 // Host-side proof that every address the launch can form lies inside its buffer: for each item
 // and segment, the smallest and largest offsets over (m, n, k) and over all pairs.
-static void check_bounds(const GemmDesc& g, size_t elem, bool check_c = true) {
+static void check_bounds(const GemmDesc& g, size_t elem) {
   auto base_max = [&](int mode, long long pstride) -> long long {
     if (mode == MODE_PAIR) return (long long)(g.n_pairs - 1) * pstride;
     if (mode == MODE_BRA) return (long long)g.max_bra * pstride;
@@ -283,7 +283,7 @@ static void check_bounds(const GemmDesc& g, size_t elem, bool check_c = true) {
                          (long long)(g.N - 1) * g.c_sn;
   for (int s = 0; s < g.st.n_sub; ++s) {
     const long long c0 = g.hst->sub_c[s];
-    if (check_c && (c0 < 0 || c0 + c_hi >= g.c_len))
+    if (c0 < 0 || c0 + c_hi >= g.c_len)
       TTN_FAIL(TTN_EINVAL, "gemm bounds: C item %d reaches %lld of %lld (elem %zu)", s, c0 + c_hi,
                g.c_len, elem);
     if (g.K <= 0) continue;
@@ -1130,20 +1130,108 @@ void launch_wait_selftest(ttn_ctx* ctx, unsigned long long budget_ns) {
   CUDA_LAUNCH_CHECK();
 }
 
-// Segmented level stage, warp-specialised (float32 SIMT compute, slices stored [b][a] with
-// N = NA, i.e. already in the compute layout). Warps 0..nw-1 compute (32 rows each), warp nw
-// produces: its first lane requests segment j's A tile and slice into stage j % 2 once the
-// compute warps have released that stage (an "empty" mbarrier with one arrival per compute
-// warp), and the copies complete a "full" mbarrier the compute warps wait on. No CTA-wide
-// barrier inside the segment loop; every wait is bounded.
+// acc += this warp's 32 rows of A (shared, K rows of lda floats) x a raw slice Er[k][n] (row
+// length N = NA) on the tensor cores: mma.sync m16n8k8 TF32 with the 3xTF32 split of both
+// operands, B fragments split as they are read (the raw [k][n] slice gives conflict-free
+// fragment loads for N = 8, 16, 24, 32). lda = rows + 8 keeps the A fragment loads
+// conflict-free. acc holds the m16n8 accumulator fragments (2 m tiles x NA/8 n tiles x 4).
 template <int NA>
+__device__ __forceinline__ void level_mac_raw_tc(const float* As, int lda, const float* Er, int K,
+                                                 float* acc) {
+  constexpr int NT = NA / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gq = lane >> 2, tq = lane & 3, rw = warp * 32;
+  for (int k0 = 0; k0 < K; k0 += 8) {
+    uint32_t ah[2][4], al[2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const float* ap = As + (k0 + tq) * lda + rw + m * 16 + gq;
+      const float x[4] = {ap[0], ap[8], ap[4 * lda], ap[4 * lda + 8]};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ah[m][q] = tf32_bits(x[q]);
+        al[m][q] = tf32_bits(x[q] - __uint_as_float(ah[m][q]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const float e0 = Er[(k0 + tq) * NA + j * 8 + gq];
+      const float e1 = Er[(k0 + tq + 4) * NA + j * 8 + gq];
+      uint32_t bh[2], bl[2];
+      bh[0] = tf32_bits(e0);
+      bl[0] = tf32_bits(e0 - __uint_as_float(bh[0]));
+      bh[1] = tf32_bits(e1);
+      bl[1] = tf32_bits(e1 - __uint_as_float(bh[1]));
+#pragma unroll
+      for (int m = 0; m < 2; ++m) {
+        float* d = acc + (m * NT + j) * 4;
+        mma_m16n8k8_tf32(d, al[m], bh);
+        mma_m16n8k8_tf32(d, ah[m], bl);
+        mma_m16n8k8_tf32(d, ah[m], bh);
+      }
+    }
+  }
+}
+
+// Segmented level stage, warp-specialised (slices stored [b][a] with N = NA, i.e. already in
+// the SIMT compute layout). Warps 0..nw-1 compute (32 rows each; float32 SIMT, or the
+// tensor-core 3xTF32 path when TC), warp nw produces: its first lane requests segment j's A
+// tile and slice into stage j % 2 once the compute warps have released that stage (an "empty"
+// mbarrier with one arrival per compute warp), and the copies complete a "full" mbarrier the
+// compute warps wait on. No CTA-wide barrier inside the segment loop; every wait is bounded.
+// A tile rows are lda = rows_cta (+ 8 for TC) floats apart.
+template <int NA, bool TC>
+__device__ __forceinline__ bool seg_ws_pipeline(const GemmDesc& g, float* dsm, int rows_cta,
+                                                int lda, int stage, int pair, int s0, int nseg,
+                                                int r0, int nrow, unsigned long long* full,
+                                                unsigned long long* empty, float* acc) {
+  const int nw = rows_cta >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == nw) {
+    if (lane == 0) {
+      const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+      const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+      for (int j = 0; j < nseg; ++j) {
+        const int st = j & 1;
+        if (j >= 2 && !mbar_wait(&empty[st], ((j >> 1) - 1) & 1, g.wait_flag)) break;
+        fence_proxy_async();
+        float* As = dsm + st * stage;
+        float* Es = As + g.K * lda;
+        const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
+        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
+        for (int b = 0; b < g.K; ++b)
+          bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
+        bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
+      }
+    }
+    return false;
+  }
+  const bool live = warp * 32 < nrow;   // warp-uniform
+#pragma unroll
+  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
+  for (int j = 0; j < nseg; ++j) {
+    const int st = j & 1;
+    if (!mbar_wait(&full[st], (j >> 1) & 1, g.wait_flag)) return false;
+    const float* As = dsm + st * stage;
+    if (live) {
+      if constexpr (TC) level_mac_raw_tc<NA>(As, lda, As + g.K * lda, g.K, acc);
+      else level_mac<NA, false>(As, lda, As + g.K * lda, g.K, acc);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  return true;
+}
+
+template <int NA, bool TC>
 __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtiles, int rows_cta,
                                                            int vec_store) {
   extern __shared__ __align__(16) float dsm[];
   __shared__ __align__(8) unsigned long long full[2];
   __shared__ __align__(8) unsigned long long empty[2];
   const int nw = rows_cta >> 5;
-  const int stage = g.K * rows_cta + g.K * NA;
+  const int lda = rows_cta + (TC ? 8 : 0);
+  const int stage = g.K * lda + g.K * NA;
   const long long bid = blockIdx.x;
   const int rt = (int)(bid % rtiles);
   const long long rest = bid / rtiles;
@@ -1160,176 +1248,18 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
     mbar_init_fence();
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == nw) {
-    if (lane == 0) {
-      const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
-      const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
-      for (int j = 0; j < nseg; ++j) {
-        const int st = j & 1;
-        if (j >= 2 && !mbar_wait(&empty[st], ((j >> 1) - 1) & 1, g.wait_flag)) break;
-        fence_proxy_async();
-        float* As = dsm + st * stage;
-        float* Es = As + g.K * rows_cta;
-        const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
-        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
-        for (int b = 0; b < g.K; ++b)
-          bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
-        bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
-      }
-    }
-    return;
-  }
-  const bool live = warp * 32 < nrow;   // warp-uniform
   float acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
-  for (int j = 0; j < nseg; ++j) {
-    const int st = j & 1;
-    if (!mbar_wait(&full[st], (j >> 1) & 1, g.wait_flag)) return;
-    const float* As = dsm + st * stage;
-    if (live) level_mac<NA, false>(As, rows_cta, As + g.K * rows_cta, g.K, acc);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-  }
-  if (!live) return;
+  if (!seg_ws_pipeline<NA, TC>(g, dsm, rows_cta, lda, stage, pair, s0, nseg, r0, nrow, full,
+                               empty, acc))
+    return;
+  if ((threadIdx.x >> 5) * 32 >= nrow) return;
   long long cidx = 0;
   if (g.c_mode == MODE_PAIR) cidx = pair;
   else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
   else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
-  level_store<NA, false>(static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
-                             (long long)r0 * g.N,
-                         nrow, g.N, acc, vec_store);
-}
-
-// Named barrier over the compute warps only (the producer warp has left by then).
-__device__ __forceinline__ void compute_warps_sync(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-
-// Segmented level stage of an auxiliary node fused with the closure of its environment
-// update: the warp-specialised segment loop of level_seg_ws_kernel produces this CTA's row tile
-// of Z[slot] (rows (b_open, a_rest), columns a_last) in registers; the tile, whose rows cover
-// whole b_open values (c.grp rows each), goes to shared memory and is closed at once with the
-// bra, E[slot][a_open][b_open] = sum_k bra[a_open][k] Z[b_open][k] (k = (a_rest, a_last)), the
-// bra streamed through shared memory in chunks of kSegCloseKC. Z never reaches global memory.
-// A compute warp whose bounded wait gave up stops computing but still reaches the compute-warp
-// barrier, so every warp leaves together.
-constexpr int kSegCloseKC = 96;
-constexpr int kSegCloseMaxOut = 4;
-template <int NA>
-__global__ void __launch_bounds__(320) level_seg_close_kernel(GemmDesc g, SegClose c, int rtiles,
-                                                              int rows_cta) {
-  extern __shared__ __align__(16) float dsm[];
-  __shared__ __align__(8) unsigned long long full[2];
-  __shared__ __align__(8) unsigned long long empty[2];
-  __shared__ int failed;
-  const int nw = rows_cta >> 5;
-  const int stage = g.K * rows_cta + g.K * NA;
-  const long long bid = blockIdx.x;
-  const int rt = (int)(bid % rtiles);
-  const long long rest = bid / rtiles;
-  const int sub = (int)(rest % g.st.n_sub);
-  const int pair = (int)(rest / g.st.n_sub);
-  const int s0 = g.st.seg_ptr[sub], nseg = g.st.seg_ptr[sub + 1] - s0;
-  const int r0 = rt * rows_cta;
-  const int nrow = min(rows_cta, g.M - r0);
-  if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], nw);
-    mbar_init(&empty[1], nw);
-    mbar_init_fence();
-    failed = 0;
-  }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == nw) {
-    if (lane == 0) {
-      const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
-      const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
-      for (int j = 0; j < nseg; ++j) {
-        const int st = j & 1;
-        if (j >= 2 && !mbar_wait(&empty[st], ((j >> 1) - 1) & 1, g.wait_flag)) break;
-        fence_proxy_async();
-        float* As = dsm + st * stage;
-        float* Es = As + g.K * rows_cta;
-        const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
-        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
-        for (int b = 0; b < g.K; ++b)
-          bulk_copy_g2s(As + b * rows_cta, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
-        bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
-      }
-    }
-    return;
-  }
-  const int nthreads = nw * 32;
-  const bool live = warp * 32 < nrow;   // warp-uniform
-  float acc[NA];
-#pragma unroll
-  for (int i = 0; i < NA; ++i) acc[i] = 0.f;
-  bool ok = true;
-  for (int j = 0; j < nseg && ok; ++j) {
-    const int st = j & 1;
-    ok = mbar_wait(&full[st], (j >> 1) & 1, g.wait_flag);
-    if (!ok) break;
-    const float* As = dsm + st * stage;
-    if (live) level_mac<NA, false>(As, rows_cta, As + g.K * rows_cta, g.K, acc);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-  }
-  if (!ok && lane == 0) atomicOr(&failed, 1);
-  compute_warps_sync(nthreads);          // every copy has landed and every warp is done
-  if (failed) return;
-  // this warp's rows of the Z tile -> shared memory, row stride N (= NA)
-  float* Zs = dsm;
-  if (live) {
-    constexpr int CPT = NA / 4;
-    const int rl = warp * 32 + (lane >> 2) * 4, cg = lane & 3;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (rl + i < nrow) {
-#pragma unroll
-        for (int cc = 0; cc < CPT; ++cc) Zs[(rl + i) * NA + cg * CPT + cc] = acc[i * CPT + cc];
-      }
-  }
-  float* Bs = dsm + stage;               // bra chunk [a_open][kSegCloseKC + 1]
-  const int K2 = c.grp * NA;             // closure contraction length
-  const int nb0 = nrow / c.grp;          // b_open values of this tile
-  const int nout = c.da * nb0;
-  const float* bra = c.bra + (long long)g.pair_bra[pair] * c.bra_pstride;
-  float cacc[kSegCloseMaxOut];
-#pragma unroll
-  for (int q = 0; q < kSegCloseMaxOut; ++q) cacc[q] = 0.f;
-  for (int k0 = 0; k0 < K2; k0 += kSegCloseKC) {
-    const int kc = min(kSegCloseKC, K2 - k0);
-    compute_warps_sync(nthreads);        // Zs written / previous chunk consumed
-    for (int i = threadIdx.x; i < c.da * kc; i += nthreads) {
-      const int a = i / kc, k = i - a * kc;
-      Bs[a * (kSegCloseKC + 1) + k] = bra[(long long)a * K2 + k0 + k];
-    }
-    compute_warps_sync(nthreads);
-#pragma unroll
-    for (int q = 0; q < kSegCloseMaxOut; ++q) {
-      const int o = threadIdx.x + q * nthreads;
-      if (o >= nout) break;
-      const int a = o % c.da, b0l = o / c.da;
-      const float* zr = Zs + b0l * K2 + k0;
-      const float* br = Bs + a * (kSegCloseKC + 1);
-      float s = 0.f;
-      for (int k = 0; k < kc; ++k) s = fmaf(br[k], zr[k], s);
-      cacc[q] += s;
-    }
-  }
-  const int b00 = r0 / c.grp;
-  float* out = c.out + (long long)pair * c.out_pstride + (long long)sub * c.da * c.db;
-#pragma unroll
-  for (int q = 0; q < kSegCloseMaxOut; ++q) {
-    const int o = threadIdx.x + q * nthreads;
-    if (o >= nout) break;
-    const int a = o % c.da, b0l = o / c.da;
-    out[(long long)a * c.db + b00 + b0l] = cacc[q];
-  }
+  level_store<NA, TC>(static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] +
+                          (long long)r0 * g.N,
+                      nrow, g.N, acc, vec_store);
 }
 
 namespace {
@@ -1380,73 +1310,6 @@ static bool level_tma_ok(const GemmDesc& g) {
   return g.hst->a4 && g.hst->b4;
 }
 
-// Rows per CTA of the fused segmented-level + closure kernel: whole warps, whole b_open groups
-// of grp rows, at most 9 compute warps, balanced over the row tiles; 0 if none fits.
-static int seg_close_rows(int M, int grp) {
-  if (grp <= 0 || M % grp != 0) return 0;
-  int best = 0;
-  for (int r = 32; r <= 288; r += 32)
-    if (r % grp == 0) best = r;
-  if (best == 0) return 0;
-  const int tiles = (M + best - 1) / best;
-  const int per = (M / grp + tiles - 1) / tiles * grp;      // b_open groups split evenly
-  for (int r = 32; r <= best; r += 32)
-    if (r % grp == 0 && r >= per) return r;
-  return best;
-}
-
-bool seg_close_ok(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c) {
-  if (ctx->tf32x3 || !level_tma_ok(g) || g.st.n_grp != 0) return false;
-  const int na = level_tma_na(g.N);
-  if (na != g.N || !(g.b_sn == 1 && g.b_sk == g.N && g.K != 1)) return false;
-  const int rows = seg_close_rows(g.M, c.grp);
-  if (rows == 0 || c.grp * c.db != g.M) return false;
-  if ((long long)c.da * (rows / c.grp) > (long long)kSegCloseMaxOut * rows) return false;
-  const size_t stage = (size_t)g.K * rows + (size_t)g.K * na;
-  if ((size_t)rows * na > stage || (size_t)c.da * (kSegCloseKC + 1) > stage) return false;
-  return sizeof(float) * 2 * stage <= kLevelTmaSmem;
-}
-
-void launch_level_seg_close(ttn_ctx* ctx, const GemmDesc& g, const SegClose& c, long long out_len,
-                            long long bra_len) {
-  if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
-  TTN_REQUIRE(seg_close_ok(ctx, g, c), "fused level + closure: unsupported shape");
-  check_bounds(g, sizeof(float), false);     // A and B; the output is checked below
-  const long long K2 = (long long)c.grp * g.N;
-  TTN_REQUIRE((long long)(g.n_pairs - 1) * c.out_pstride + (long long)g.st.n_sub * c.da * c.db <=
-                  out_len,
-              "fused closure bounds: output");
-  TTN_REQUIRE((long long)g.max_bra * c.bra_pstride + c.da * K2 <= bra_len,
-              "fused closure bounds: bra");
-  const int na = level_tma_na(g.N);
-  const int rows_cta = seg_close_rows(g.M, c.grp);
-  const int rt = (g.M + rows_cta - 1) / rows_cta;
-  const long long grid = (long long)rt * g.st.n_sub * g.n_pairs;
-  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
-  const double flops = 2.0 * g.M * g.N * (double)g.K * g.hst->n_seg * g.n_pairs +
-                       2.0 * c.da * c.db * (double)K2 * g.st.n_sub * g.n_pairs;
-  const double bytes = algorithmic_bytes(g, sizeof(float)) +
-                       4.0 * std::min(g.n_pairs, g.max_bra + 1) * c.da * K2 +
-                       4.0 * g.n_pairs * g.st.n_sub * c.da * c.db;
-  static const char* nm[] = {"level_seg_close_f32_8", "level_seg_close_f32_16",
-                             "level_seg_close_f32_24", "level_seg_close_f32_32"};
-  LaunchScope ls(ctx, nm[na / 8 - 1], flops, bytes);
-  GemmDesc gd = g;
-  gd.wait_flag = ctx->d_wait;
-  const size_t smem = sizeof(float) * 2 * ((size_t)g.K * rows_cta + (size_t)g.K * na);
-  auto go = [&](auto kern) {
-    smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
-    kern<<<(unsigned)grid, rows_cta + 32, smem, ctx->stream>>>(gd, c, rt, rows_cta);
-  };
-  switch (na) {
-    case 8: go(level_seg_close_kernel<8>); break;
-    case 16: go(level_seg_close_kernel<16>); break;
-    case 24: go(level_seg_close_kernel<24>); break;
-    default: go(level_seg_close_kernel<32>); break;
-  }
-  CUDA_LAUNCH_CHECK();
-}
-
 template <class T>
 void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   if (g.n_pairs <= 0 || g.st.n_sub <= 0 || g.M <= 0 || g.N <= 0) return;
@@ -1478,19 +1341,30 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
     const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
-    if (!tc && et && g.N == na) {
-      // slices already in the compute layout: warp-specialised copy/compute pipeline
-      const size_t smem_ws = sizeof(float) * 2 * ((size_t)g.K * rows_cta + (size_t)g.K * na);
+    if (et && g.N == na) {
+      // slices already in the SIMT compute layout: warp-specialised copy/compute pipeline
+      // (float32 SIMT, or 3xTF32 tensor cores with A rows padded by 8 floats)
+      const size_t lda = (size_t)rows_cta + (tc ? 8 : 0);
+      const size_t smem_ws = sizeof(float) * 2 * ((size_t)g.K * lda + (size_t)g.K * na);
       auto go_ws = [&](auto kern) {
         smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
         kern<<<(unsigned)grid, rows_cta + 32, smem_ws, ctx->stream>>>(gd, rt, rows_cta,
                                                                         vec ? 1 : 0);
       };
-      switch (na) {
-        case 8: go_ws(level_seg_ws_kernel<8>); break;
-        case 16: go_ws(level_seg_ws_kernel<16>); break;
-        case 24: go_ws(level_seg_ws_kernel<24>); break;
-        default: go_ws(level_seg_ws_kernel<32>); break;
+      if (tc) {
+        switch (na) {
+          case 8: go_ws(level_seg_ws_kernel<8, true>); break;
+          case 16: go_ws(level_seg_ws_kernel<16, true>); break;
+          case 24: go_ws(level_seg_ws_kernel<24, true>); break;
+          default: go_ws(level_seg_ws_kernel<32, true>); break;
+        }
+      } else {
+        switch (na) {
+          case 8: go_ws(level_seg_ws_kernel<8, false>); break;
+          case 16: go_ws(level_seg_ws_kernel<16, false>); break;
+          case 24: go_ws(level_seg_ws_kernel<24, false>); break;
+          default: go_ws(level_seg_ws_kernel<32, false>); break;
+        }
       }
       CUDA_LAUNCH_CHECK();
       return;

@@ -1589,6 +1589,57 @@ static std::vector<std::vector<int>> clusters_by_gap(const std::vector<double>& 
   return out;
 }
 
+// Rayleigh-Ritz over the states of Y and refit (the orthogonalisation step of Alg. 3, and the
+// generalized eigenvalue problem Hc = ESc of Sec. III.B over a whole block): H~ and M~ over Y,
+// canonical orthogonalisation (eigenvalues of M~ below rr_eps * max dropped), X_a = the fitted
+// sum_b v_ba Y_b of the a-th Ritz vector (fit starts from the Y_b of largest |v_ba|),
+// normalised. theta receives the Ritz values; X and Y hold the same number of states.
+template <class T>
+static void rr_refit(ttn_ctx* ctx, ttn_ttno* H, ttn_ttno* Id, const ttn_block* Y, ttn_block* X,
+                     double rr_eps, int fit_sweeps, int prec, std::vector<double>& theta) {
+  cudaStream_t st = ctx->stream;
+  const int m = Y->n_states;
+  DevBuf Ht((size_t)m * m * sizeof(double), st), Mt((size_t)m * m * sizeof(double), st),
+      th((size_t)m * sizeof(double), st), V((size_t)m * m * sizeof(double), st);
+  CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
+  CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
+  if (gram_device(ctx, H, Y, Y, Ht.as<double>(), m, prec) +
+      gram_device(ctx, Id, Y, Y, Mt.as<double>(), m, prec))
+    TTN_FAIL(TTN_ENONFINITE, "Rayleigh-Ritz of a block: non-finite Gram entries");
+  rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), m, rr_eps, th.as<double>(),
+                       V.as<double>());
+  std::vector<double> hV((size_t)m * m);
+  theta.assign(m, 0.0);
+  CUDA_CHECK(cudaMemcpyAsync(theta.data(), th.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CUDA_CHECK(cudaMemcpyAsync(hV.data(), V.p, hV.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             st));
+  CUDA_CHECK(cudaStreamSynchronize(st));
+  FitGroup g{Id, Y, {}, {}, {}};
+  std::vector<int> init(m);
+  for (int a = 0; a < m; ++a) {
+    int arg = 0;
+    double best = -1.0;
+    for (int b = 0; b < m; ++b) {
+      const double v = hV[(size_t)b * m + a];
+      if (std::fabs(v) > best) {
+        best = std::fabs(v);
+        arg = b;
+      }
+      if (v != 0.0) {
+        g.out_j.push_back(a);
+        g.in_k.push_back(b);
+        g.coef.push_back(v);
+      }
+    }
+    init[a] = arg;
+  }
+  ttn_status cs = ttn_block_copy_states(X, Y, m, init.data());
+  if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+  std::vector<FitGroup> gs{g};
+  fit_impl<T>(ctx, gs, X, fit_sweeps);
+  normalize_states<T>(ctx, X, prec);
+}
+
 // Block inverse iteration (Alg. 3): every block uses the mean Rayleigh quotient of its states as
 // the shift; every state is solved by ALS; blocks of more than one state are re-orthogonalised
 // by their own Rayleigh-Ritz step and refitted.
@@ -1653,44 +1704,8 @@ static void inverse_iteration_impl(ttn_ctx* ctx, ttn_ttno* H, ttn_block* x, int 
       auto Yc = new_block(m), Xc = new_block(m);
       ttn_status cs = ttn_block_copy_states(Yc.get(), Y.get(), m, c.data());
       if (cs != TTN_OK) TTN_FAIL(cs, "copy");
-      DevBuf Ht((size_t)m * m * sizeof(double), st), Mt((size_t)m * m * sizeof(double), st),
-          th((size_t)m * sizeof(double), st), V((size_t)m * m * sizeof(double), st);
-      CUDA_CHECK(cudaMemsetAsync(Ht.p, 0, (size_t)m * m * sizeof(double), st));
-      CUDA_CHECK(cudaMemsetAsync(Mt.p, 0, (size_t)m * m * sizeof(double), st));
-      if (gram_device(ctx, H, Yc.get(), Yc.get(), Ht.as<double>(), m, prec) +
-          gram_device(ctx, Id, Yc.get(), Yc.get(), Mt.as<double>(), m, prec))
-        TTN_FAIL(TTN_ENONFINITE, "inverse iteration %d: non-finite block Gram", it);
-      rayleigh_ritz_device(ctx, m, Ht.as<double>(), Mt.as<double>(), m, rr_eps, th.as<double>(),
-                           V.as<double>());
-      std::vector<double> hth(m), hV((size_t)m * m);
-      CUDA_CHECK(cudaMemcpyAsync(hth.data(), th.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
-      CUDA_CHECK(cudaMemcpyAsync(hV.data(), V.p, hV.size() * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
-      CUDA_CHECK(cudaStreamSynchronize(st));
-      FitGroup g{Id, Yc.get(), {}, {}, {}};
-      std::vector<int> init(m);
-      for (int a = 0; a < m; ++a) {
-        int arg = 0;
-        double best = -1.0;
-        for (int b = 0; b < m; ++b) {
-          const double v = hV[(size_t)b * m + a];
-          if (std::fabs(v) > best) {
-            best = std::fabs(v);
-            arg = b;
-          }
-          if (v != 0.0) {
-            g.out_j.push_back(a);
-            g.in_k.push_back(b);
-            g.coef.push_back(v);
-          }
-        }
-        init[a] = arg;
-      }
-      cs = ttn_block_copy_states(Xc.get(), Yc.get(), m, init.data());
-      if (cs != TTN_OK) TTN_FAIL(cs, "copy");
-      std::vector<FitGroup> gs{g};
-      fit_impl<T>(ctx, gs, Xc.get(), fit_sweeps);
-      normalize_states<T>(ctx, Xc.get(), prec);
+      std::vector<double> hth;
+      rr_refit<T>(ctx, H, Id, Yc.get(), Xc.get(), rr_eps, fit_sweeps, prec, hth);
       for (int a = 0; a < m; ++a) {
         lam_n[c[a]] = hth[a];
         for (int t = 0; t < tr.n; ++t)
@@ -1891,6 +1906,37 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
     ctx->last_error = "a local MINRES solve reached minres_max before its tolerance (results "
                       "written)";
     return TTN_ENOTCONV;
+  });
+}
+
+ttn_status ttn_block_rayleigh_ritz(ttn_ctx* ctx, const ttn_ttno* Hc, ttn_block* x, double eps,
+                                   int fit_sweeps, ttn_precision prec, double* theta) {
+  if (!ctx || !Hc || !x) return TTN_EINVAL;
+  return guarded_s(ctx, [&]() -> ttn_status {
+    PrecisionScope prec_scope(ctx, prec);
+    ttn_ttno* H = const_cast<ttn_ttno*>(Hc);
+    TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
+    TTN_REQUIRE(x->n_states >= 1 && fit_sweeps >= 1 && eps >= 0.0, "bad arguments");
+    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    ttn_ttno* Id = identity_for(ctx, x->tree);
+    ttn_block* yb = nullptr;
+    {
+      ttn_tree tmp;
+      tmp.ctx = ctx;
+      tmp.info = x->tree;
+      ttn_status cs = ttn_block_create(ctx, &tmp, x->n_states, x->bond.data(), &yb);
+      if (cs != TTN_OK) TTN_FAIL(cs, "%s", ctx->last_error.c_str());
+    }
+    std::unique_ptr<ttn_block> Y(yb);
+    std::vector<int> id(x->n_states);
+    std::iota(id.begin(), id.end(), 0);
+    ttn_status cs = ttn_block_copy_states(Y.get(), x, x->n_states, id.data());
+    if (cs != TTN_OK) TTN_FAIL(cs, "copy");
+    std::vector<double> th;
+    if (prec == TTN_FP64) rr_refit<double>(ctx, H, Id, Y.get(), x, eps, fit_sweeps, prec, th);
+    else rr_refit<float>(ctx, H, Id, Y.get(), x, eps, fit_sweeps, prec, th);
+    if (theta) std::copy(th.begin(), th.end(), theta);
+    return TTN_OK;
   });
 }
 

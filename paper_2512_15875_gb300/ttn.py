@@ -72,6 +72,7 @@ _SIGS = {
     "ttn_selftest_bounded_wait": (_I, [_P, _D]),
     "ttn_iteration_times": (_I, [_P, _DP, _I]),
     "ttn_ttno_rank_bounds": (_I, [_P, _IP]),
+    "ttn_block_rayleigh_ritz": (_I, [_P, _P, _P, _D, _I, _I, _DP]),
     "ttn_fault_inject_alloc": (None, [_LL]),
 }
 
@@ -479,6 +480,15 @@ def ttn_rayleigh_ritz_noalloc(ctx, m, Ht_ptr, Mt_ptr, n, eps, theta_ptr, V_ptr):
     if st not in (0, 5):
         ctx.check(st)
     return st
+
+
+def ttn_block_rayleigh_ritz(ctx, H, x, eps=1e-12, fit_sweeps=2, prec="fp64"):
+    """Hc = ESc over all states of x (x is replaced by the fitted Ritz vectors); returns the
+    Ritz values."""
+    theta = np.zeros(x.n_states)
+    ctx.check(load().ttn_block_rayleigh_ritz(ctx.ptr, H.ptr, x.ptr, float(eps), int(fit_sweeps),
+                                             _prec(prec), _dp(theta)))
+    return theta
 
 
 def ttn_lobpcg(ctx, H, x, n_iter, shift_offset, als_sweeps=2, minres_max=10, minres_tol=1e-5,

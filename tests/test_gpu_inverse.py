@@ -79,3 +79,24 @@ def test_inverse_iteration_converges_to_eigenvalues_at_full_bond(T, ctx, gap):
     hist = T.ttn_inverse_iteration(ctx, H, bX, 6, cluster_gap=gap, als_sweeps=2, minres_max=300,
                                    minres_tol=1e-12, prec="fp64")
     assert np.abs(np.sort(hist[-1]) - ev[:5]).max() <= 1e-10 * ev[0]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_block_rayleigh_ritz_matches_oracle(T, ctx, prec):
+    # the generalized eigenvalue problem Hc = ESc over all states (Sec. III.B) on truncated,
+    # non-orthogonal states of the four-mode model
+    w = I.make_workload("c1", D=8)
+    th = T.ttn_tree_create(ctx, w.tree)
+    H, _ = T.ttn_build_ttno(ctx, th, w.ham.flat(w.tree))
+    blk = w.block(noise=5e-2)
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    theta = T.ttn_block_rayleigh_ritz(ctx, H, bX, eps=1e-12, fit_sweeps=2, prec=prec)
+    otn = N.build_ttno(w.tree, w.ham)
+    ref, Y = S.block_rayleigh_ritz(w.tree, otn, [[t[j] for t in blk] for j in range(5)], 2)
+    tol = {"fp64": 1e-10, "fp32": 2e-6}[prec]
+    assert np.abs(theta - ref).max() <= tol * abs(ref[0])
+    # the fitted Ritz vectors: same overlaps as the oracle's (not exactly the identity at this
+    # truncated bond)
+    S2, _ = T.ttn_gram(ctx, H, bX, bX)
+    M = np.array([[N.overlap(w.tree, a, b) for b in Y] for a in Y])
+    assert np.abs(S2 - M).max() <= {"fp64": 1e-9, "fp32": 1e-5}[prec]

@@ -370,3 +370,22 @@ def test_inverse_iteration_reaches_the_lowest_dense_eigenvalues(gap):
     lam, _, _ = S.inverse_iteration(w.tree, T, X0, 6, clusters, als_sweeps=2, minres_max=300,
                                     minres_tol=1e-12)
     assert np.abs(np.sort(lam) - ev[:5]).max() <= 1e-10 * ev[0]
+
+
+def test_block_rayleigh_ritz_is_the_dense_generalized_eigenproblem_at_full_bond():
+    # Hc = ESc over five non-orthogonal states (Sec. III.B): at full bond (fitting exact) the
+    # Ritz values are the generalized eigenvalues of the dense projections and the new states
+    # are orthonormal and diagonalise H
+    import scipy.linalg
+    w = I.make_workload("c1", D=36)
+    T = N.build_ttno(w.tree, w.ham)
+    H = N.dense_hamiltonian(w.ham)
+    blk = w.block(noise=5e-2)
+    X = [[t[j] for t in blk] for j in range(5)]
+    V = np.array([N.ttns_to_dense(w.tree, x) for x in X]).T
+    ref = scipy.linalg.eigh(V.T @ H @ V, V.T @ V, eigvals_only=True)
+    theta, Y = S.block_rayleigh_ritz(w.tree, T, X, fit_sweeps=2)
+    assert np.abs(theta - ref).max() <= 1e-10 * abs(ref[0])
+    D = np.array([N.ttns_to_dense(w.tree, y) for y in Y]).T
+    assert np.abs(D.T @ D - np.eye(5)).max() <= 1e-10
+    assert np.abs(D.T @ H @ D - np.diag(theta)).max() <= 1e-9 * abs(ref[0])
