@@ -476,38 +476,44 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
 }
 
 // Cyclic Jacobi across the whole grid (cooperative launch; all CTAs resident). Each round of the
-// round-robin ordering rotates m/2 disjoint index pairs: phase 1 computes every pair's rotation
-// from the current A; phase 2 applies A <- J^T A J block by block (each 2 x 2 block (P, Q)
-// depends only on its own four entries and the rotations of P and Q) and V <- V J row by row.
-// The off-diagonal norm is reduced deterministically (per-CTA partials, summed in CTA order).
+// round-robin ordering rotates m/2 disjoint index pairs. Every CTA computes all of the round's
+// rotations from the current A into its shared memory (they are cheap and identical
+// everywhere), then applies its share of A' = J^T A J block by block (each 2 x 2 block (P, Q)
+// depends only on its own four entries and the rotations of P and Q) into the other buffer of
+// a double-buffered A, and V <- V J row by row in place: one grid barrier per round. The
+// off-diagonal norm is reduced deterministically (per-CTA partials, summed in CTA order).
 struct JacobiArgs {
-  double* A;
+  double* A;        // input matrix; on return the rotated matrix (diagonal = eigenvalues)
+  double* A2;       // second buffer, m x m
   double* V;
   int m;
   int max_sweeps;
   double tol;
-  double* cs;       // [npairs]
-  double* sn;       // [npairs]
-  int* pp;          // [npairs]
-  int* qq;          // [npairs]
   double* partial;  // [2 * gridDim.x]
   int* done;        // [1]
 };
 
 __global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiArgs a) {
   cg::grid_group grid = cg::this_grid();
+  extern __shared__ double jsh[];
   const int m = a.m;
   const int mp = m + (m & 1);
   const int npairs = mp / 2;
+  double* s_cs = jsh;
+  double* s_sn = jsh + npairs;
+  int* s_pp = reinterpret_cast<int*>(jsh + 2 * npairs);
+  int* s_qq = s_pp + npairs;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gstride = (long long)gridDim.x * blockDim.x;
   __shared__ double red[33];
+  double* A = a.A;
+  double* B = a.A2;
   for (long long idx = gtid; idx < (long long)m * m; idx += gstride)
     a.V[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (long long idx = gtid; idx < (long long)m * m; idx += gstride) {
-      const double v = a.A[idx];
+      const double v = A[idx];
       tot += v * v;
       if (idx / m != idx % m) off += v * v;
     }
@@ -529,14 +535,14 @@ __global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiArgs a) {
     grid.sync();
     if (a.done[0]) break;
     for (int r = 0; r < mp - 1; ++r) {
-      for (long long i = gtid; i < npairs; i += gstride) {
+      for (int i = threadIdx.x; i < npairs; i += blockDim.x) {
         int p, q;
         if (i == 0) {
           p = 0;
           q = (r % (mp - 1)) + 1;
         } else {
-          p = (int)((i + r) % (mp - 1)) + 1;
-          q = (int)((mp - 1 - i + r) % (mp - 1)) + 1;
+          p = (i + r) % (mp - 1) + 1;
+          q = (mp - 1 - i + r) % (mp - 1) + 1;
         }
         if (p > q) {
           const int t = p;
@@ -545,48 +551,54 @@ __global__ void __launch_bounds__(256) jacobi_grid_kernel(JacobiArgs a) {
         }
         double c = 1.0, sv = 0.0;
         if (q < m) {
-          const double apq = a.A[(long long)p * m + q];
+          const double apq = A[(long long)p * m + q];
           if (apq != 0.0) {
-            const double theta = (a.A[(long long)q * m + q] - a.A[(long long)p * m + p]) / (2.0 * apq);
+            const double theta = (A[(long long)q * m + q] - A[(long long)p * m + p]) / (2.0 * apq);
             const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
             c = 1.0 / sqrt(t * t + 1.0);
             sv = t * c;
           }
         }
-        a.pp[i] = p;
-        a.qq[i] = q;
-        a.cs[i] = c;
-        a.sn[i] = sv;
+        s_pp[i] = p;
+        s_qq[i] = q;
+        s_cs[i] = c;
+        s_sn[i] = sv;
       }
-      grid.sync();
+      __syncthreads();
       for (long long idx = gtid; idx < (long long)npairs * npairs; idx += gstride) {
         const int P = (int)(idx / npairs), Q = (int)(idx % npairs);
-        const int p1 = a.pp[P], q1 = a.qq[P], p2 = a.pp[Q], q2 = a.qq[Q];
-        const double c1 = a.cs[P], s1 = a.sn[P], c2 = a.cs[Q], s2 = a.sn[Q];
+        const int p1 = s_pp[P], q1 = s_qq[P], p2 = s_pp[Q], q2 = s_qq[Q];
+        const double c1 = s_cs[P], s1 = s_sn[P], c2 = s_cs[Q], s2 = s_sn[Q];
         const bool hq1 = q1 < m, hq2 = q2 < m;
-        const double x00 = a.A[(long long)p1 * m + p2];
-        const double x01 = hq2 ? a.A[(long long)p1 * m + q2] : 0.0;
-        const double x10 = hq1 ? a.A[(long long)q1 * m + p2] : 0.0;
-        const double x11 = (hq1 && hq2) ? a.A[(long long)q1 * m + q2] : 0.0;
+        const double x00 = A[(long long)p1 * m + p2];
+        const double x01 = hq2 ? A[(long long)p1 * m + q2] : 0.0;
+        const double x10 = hq1 ? A[(long long)q1 * m + p2] : 0.0;
+        const double x11 = (hq1 && hq2) ? A[(long long)q1 * m + q2] : 0.0;
         // rows (J^T A), then columns (A J)
         const double r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
         const double r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
-        a.A[(long long)p1 * m + p2] = c2 * r00 - s2 * r01;
-        if (hq2) a.A[(long long)p1 * m + q2] = s2 * r00 + c2 * r01;
-        if (hq1) a.A[(long long)q1 * m + p2] = c2 * r10 - s2 * r11;
-        if (hq1 && hq2) a.A[(long long)q1 * m + q2] = s2 * r10 + c2 * r11;
+        B[(long long)p1 * m + p2] = c2 * r00 - s2 * r01;
+        if (hq2) B[(long long)p1 * m + q2] = s2 * r00 + c2 * r01;
+        if (hq1) B[(long long)q1 * m + p2] = c2 * r10 - s2 * r11;
+        if (hq1 && hq2) B[(long long)q1 * m + q2] = s2 * r10 + c2 * r11;
       }
       for (long long idx = gtid; idx < (long long)m * npairs; idx += gstride) {
         const int row = (int)(idx / npairs), Q = (int)(idx % npairs);
-        const int p2 = a.pp[Q], q2 = a.qq[Q];
+        const int p2 = s_pp[Q], q2 = s_qq[Q];
         if (q2 >= m) continue;
-        const double c2 = a.cs[Q], s2 = a.sn[Q];
+        const double c2 = s_cs[Q], s2 = s_sn[Q];
         const double vp = a.V[(long long)row * m + p2], vq = a.V[(long long)row * m + q2];
         a.V[(long long)row * m + p2] = c2 * vp - s2 * vq;
         a.V[(long long)row * m + q2] = s2 * vp + c2 * vq;
       }
       grid.sync();
+      double* t = A;
+      A = B;
+      B = t;
     }
+  }
+  if (A != a.A) {   // an odd number of rounds ended in the second buffer
+    for (long long idx = gtid; idx < (long long)m * m; idx += gstride) a.A[idx] = A[idx];
   }
 }
 
@@ -677,16 +689,23 @@ __global__ void symmetrize_kernel(double* A, int m) {
 // host-side drivers
 // ------------------------------------------------------------------------------------------------
 // Scratch (in doubles) of one grid Jacobi solve of size m: rotations, pairs, partial sums.
-static size_t jacobi_scratch_doubles(int m) {
-  const int np = (m + 1) / 2 + 1;
-  return (size_t)4 * np + 2 * 1024 + 8;
+static size_t jacobi_scratch_doubles(int m) { return (size_t)m * m + 2 * 1024 + 8; }
+
+// Shared memory of jacobi_grid_kernel: the round's rotations (cos, sin, p, q per pair).
+static size_t jacobi_smem(int m) {
+  const int npairs = (m + (m & 1)) / 2;
+  return (size_t)npairs * (2 * sizeof(double) + 2 * sizeof(int));
 }
+constexpr int kJacobiMaxM = 2048;
 
 static int jacobi_grid_blocks(int device) {
   static int cached[64] = {0};
   if (device >= 0 && device < 64 && cached[device]) return cached[device];
   int per_sm = 0, sms = 0;
-  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel, 256, 0));
+  CUDA_CHECK(cudaFuncSetAttribute(jacobi_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)jacobi_smem(kJacobiMaxM)));
+  CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel, 256,
+                                                           jacobi_smem(kJacobiMaxM)));
   CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   int b = std::max(1, std::min(per_sm, 2) * sms);
   b = std::min(b, 1024);
@@ -697,23 +716,20 @@ static int jacobi_grid_blocks(int device) {
 // Eigen-decomposition of the symmetric m x m matrix A (destroyed: diagonal = eigenvalues) with
 // eigenvectors in the columns of V, on the whole GPU. scratch: jacobi_scratch_doubles(m).
 static void launch_jacobi_grid(ttn_ctx* ctx, double* A, double* V, int m, double* scratch) {
-  const int np = (m + 1) / 2 + 1;
+  TTN_REQUIRE(m <= kJacobiMaxM, "Jacobi eigensolver: m = %d above %d", m, kJacobiMaxM);
   JacobiArgs a;
   a.A = A;
+  a.A2 = scratch;
   a.V = V;
   a.m = m;
   a.max_sweeps = 40;
   a.tol = 1e-15;
-  a.cs = scratch;
-  a.sn = scratch + np;
-  a.pp = reinterpret_cast<int*>(scratch + 2 * np);
-  a.qq = reinterpret_cast<int*>(scratch + 3 * np);
-  a.partial = scratch + 4 * np;
-  a.done = reinterpret_cast<int*>(scratch + 4 * np + 2 * 1024);
+  a.partial = scratch + (size_t)m * m;
+  a.done = reinterpret_cast<int*>(scratch + (size_t)m * m + 2 * 1024);
   const int blocks = jacobi_grid_blocks(ctx->device);
   void* args[] = {&a};
   CUDA_CHECK(cudaLaunchCooperativeKernel((const void*)jacobi_grid_kernel, dim3(blocks), dim3(256),
-                                         args, 0, ctx->stream));
+                                         args, jacobi_smem(m), ctx->stream));
 }
 
 

@@ -33,7 +33,8 @@ import numpy as np
 
 __all__ = [
     "Tree", "Hamiltonian", "Workload",
-    "ho_matrices", "mps_tree", "fork_tree", "leaf_only_binary_tree", "all_physical_binary_tree",
+    "ho_matrices", "mps_tree", "fork_tree", "t_tree", "leaf_only_binary_tree",
+    "all_physical_binary_tree",
     "cap_bonds", "uniform_bonds", "coupled_oscillators", "quartic_force_field",
     "uniform_coupled_model", "lowest_harmonic_configurations", "initial_block",
     "make_workload", "WORKLOADS", "src_sketch",
@@ -115,6 +116,28 @@ def fork_tree(n_backbone: int, chain_len: int, d: int) -> Tree:
             prev = len(parent) - 1
             m += 1
     return Tree(parent, phys, mode, name=f"fork{n_backbone}x{chain_len}")
+
+
+def t_tree(n_modes: int, d: int) -> Tree:
+    """T tree (Appendix B): an auxiliary centre node (node 0, the root) with three chains of
+    physical nodes hanging off it; the modes are split into three nearly equal consecutive runs
+    and each chain starts at the mode next to the centre (the end of its run for the first
+    chain, the start for the others, as in the figure of the 64-mode T tree)."""
+    sizes = [n_modes // 3 + (1 if k < n_modes % 3 else 0) for k in range(3)]
+    runs, m0 = [], 0
+    for sz in sizes:
+        runs.append(list(range(m0, m0 + sz)))
+        m0 += sz
+    runs[0] = runs[0][::-1]
+    parent, phys, mode = [-1], [0], [-1]
+    for run in runs:
+        prev = 0
+        for m in run:
+            parent.append(prev)
+            phys.append(d)
+            mode.append(m)
+            prev = len(parent) - 1
+    return Tree(parent, phys, mode, name=f"ttree{n_modes}")
 
 
 def leaf_only_binary_tree(depth: int, d: int) -> Tree:

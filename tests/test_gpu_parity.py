@@ -67,6 +67,7 @@ CASES = [
     ("fork2x2_D24", lambda: I.fork_tree(2, 2, 5), 5, 24),
     ("leafbin2_D20", lambda: I.leaf_only_binary_tree(2, 5), 5, 20),
     ("physbin6_D17", lambda: I.all_physical_binary_tree(6, 4), 4, 17),
+    ("ttree6_D16", lambda: I.t_tree(6, 4), 4, 16),
 ]
 
 

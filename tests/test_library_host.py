@@ -54,6 +54,8 @@ TREES = [
     ("leafbin2", lambda d: I.leaf_only_binary_tree(2, d)),
     ("physbin5", lambda d: I.all_physical_binary_tree(5, d)),
     ("physbin6", lambda d: I.all_physical_binary_tree(6, d)),
+    ("ttree5", lambda d: I.t_tree(5, d)),
+    ("fork3x1", lambda d: I.fork_tree(3, 1, d)),
 ]
 
 

@@ -30,6 +30,7 @@ SMALL_TREES = [
     ("fork2x2", lambda d: I.fork_tree(2, 2, d)),
     ("leafbin2", lambda d: I.leaf_only_binary_tree(2, d)),
     ("physbin5", lambda d: I.all_physical_binary_tree(5, d)),
+    ("ttree5", lambda d: I.t_tree(5, d)),
 ]
 
 
