@@ -3,7 +3,7 @@
 Test infrastructure only (see the package docstring). Environments are recomputed from scratch
 for every local step: slow, and obviously the definition.
 
-Readings of points the paper leaves open (each is listed with its reason in the design notes):
+Readings of points the paper leaves open:
 * gauge: the solution TTNS is kept in canonical form with the orthogonality centre at the node
   being updated (QR moves, R with a non-negative diagonal), so the fitting metric is I and ALS
   solves (H_eff - s I) y_t = b_t;
