@@ -15,6 +15,7 @@
 // local operators, close with the bra" of Sec. II.C (Figs. variational and als), with the TTNO
 // kept block-sparse: only distinct (w-prefix) and (prefix, w_open) combinations are contracted.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <set>
@@ -337,6 +338,44 @@ void node_op(ttn_ctx* ctx, ttn_ttno* H, int t, int open, const ttn_block* bra,
   std::vector<long long> sizes;
   DevTables& tab = get_tables(H, p, Da, Db, d, out_kind, sizes);
   cudaStream_t st = ctx->stream;
+
+  // The intermediates T_l and Z grow with the number of pairs; beyond the workspace budget
+  // (TTN_WORKSPACE_GB, default 24 GB) the pairs are contracted in consecutive chunks, each
+  // reading its own slice of the environments and writing its own slice of the output.
+  {
+    long long per_pair = 0;
+    const int n_levels = p.fused ? mC - 1 : mC;
+    for (int l = 1; l <= n_levels; ++l) per_pair += (long long)p.level[l - 1].size() * sizes[l];
+    if (p.fused && mC >= 1) {
+      const int c = p.C[mC - 1];
+      per_pair += (long long)p.fG_prefix.size() * Da[c] * Db[c];
+    }
+    if (out_kind != OUT_LOCAL) per_pair += (long long)p.n_slots * sizes[mC];
+    per_pair *= (long long)sizeof(T);
+    const char* env_gb = getenv("TTN_WORKSPACE_GB");
+    const double budget = (env_gb ? atof(env_gb) : 24.0) * 1e9;
+    const long long chunk = std::max<long long>(1, (long long)(budget / std::max<long long>(per_pair, 1)));
+    if (P > chunk) {
+      long long out_per_pair = 0;
+      if (out_kind == OUT_ENV) out_per_pair = (long long)p.n_slots * Da[open] * Db[open];
+      else if (out_kind == OUT_LOCAL) out_per_pair = (long long)p.n_slots * sizes[mC];
+      else {
+        out_per_pair = 1;
+      }
+      const size_t out_elem = out_kind == OUT_SCALAR ? sizeof(double) : sizeof(T);
+      for (long long c0 = 0; c0 < P; c0 += chunk) {
+        const int Pc = (int)std::min<long long>(chunk, P - c0);
+        PairSet pc{Pc, ps.d_pb + c0, ps.d_pk + c0, ps.max_bra, ps.max_ket};
+        std::vector<const T*> envc(env.size(), nullptr);
+        for (int m = 0; m < nl; ++m)
+          if (env[m]) envc[m] = env[m] + c0 * ((long long)Dw[m] * Da[m] * Db[m]);
+        void* outc = static_cast<char*>(out) + (size_t)(c0 * out_per_pair) * out_elem;
+        node_op<T>(ctx, H, t, open, bra, ket, pc, envc, env_da, outc,
+                   out_len - c0 * out_per_pair, out_kind, ket_ptr, ket_n);
+      }
+      return;
+    }
+  }
 
   // T_0: permuted ket of every ket state
   std::vector<int> kd(Db.begin(), Db.end());

@@ -244,3 +244,40 @@ def test_full_size_qff_gram_sampled(T, ctx, prec):
         a, b = [x[i] for x in blk], [x[j] for x in blk]
         assert abs(Hm[i, j] - N.expectation_terms(w.tree, w.ham, a, b)) <= TOL[prec] * scale
         assert abs(S[i, j] - N.overlap(w.tree, a, b)) <= TOL[prec] * np.abs(np.diag(S)).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_contractions_in_pair_chunks_match_oracle(T, ctx, prec, monkeypatch):
+    """A workspace budget far below one pair's intermediates makes every node contraction run
+    in chunks of pairs (each with its own slice of environments and outputs, ragged last
+    chunk); environments, H_eff and the Gram still match the oracle."""
+    monkeypatch.setenv("TTN_WORKSPACE_GB", "2e-6")
+    case = CASES[1]
+    tree, ham, bonds, th, otn, H, A, B, bA, bB = _setup(T, ctx, case, 3, 3, seed=23)
+    pb, pk = [0, 1, 2, 2, 0], [0, 2, 1, 2, 1]
+    envs = T.ttn_envs_create(ctx, th)
+    T.ttn_env_update(ctx, H, bA, bB, pb, pk, 2, envs, prec)
+    for p, (i, j) in enumerate(zip(pb, pk)):
+        up, down = N.environments(tree, otn, [x[i] for x in A], [x[j] for x in B])
+        for t in range(tree.n_nodes):
+            if t == tree.root:
+                continue
+            for direction, ref in ((0, up[t]), (1, down[t])):
+                ref = np.transpose(ref, (1, 0, 2))
+                got = T.ttn_envs_get(envs, t, direction, p, ref.shape)
+                assert _rel(got, ref) <= TOL[prec], (t, direction)
+    envs_d = T.ttn_envs_create(ctx, th)
+    T.ttn_env_update(ctx, H, bA, bA, [0, 1, 2], [0, 1, 2], 2, envs_d, prec)
+    bY = T.ttn_block_create(ctx, th, 3, bonds)
+    shp = shapes(tree, bonds)
+    for t in range(tree.n_nodes):
+        T.ttn_heff_apply(ctx, H, envs_d, t, bB, bY, prec=prec)
+        got = T.ttn_block_get(bY, -1, t).reshape((3,) + shp[t])
+        for s in range(3):
+            ref = N.heff_apply(tree, otn, t, [x[s] for x in A], B[t][s])
+            assert _rel(got[s], ref) <= TOL[prec] * 10, (t, s)
+    S, Hm = T.ttn_gram(ctx, H, bA, bB, prec=prec)
+    for i in range(3):
+        for j in range(3):
+            a, b = [x[i] for x in A], [x[j] for x in B]
+            assert abs(Hm[i, j] - N.expectation(tree, otn, a, b)) <= 10 * TOL[prec] * np.abs(Hm).max()
