@@ -34,10 +34,11 @@ void StageHost::finalize() {
   n_seg = (long long)seg_a.size();
   single = true;
   for (size_t j = 0; j + 1 < seg_ptr.size(); ++j) single = single && seg_ptr[j + 1] - seg_ptr[j] == 1;
-  a4 = b4 = c2 = true;
+  a4 = b4 = c2 = c4 = true;
   for (long long a : seg_a) a4 = a4 && a % 4 == 0;
   for (long long b : seg_b) b4 = b4 && b % 4 == 0;
   for (long long c : sub_c) c2 = c2 && c % 2 == 0;
+  for (long long c : sub_c) c4 = c4 && c % 4 == 0;
   grp_max = 0;
   for (size_t q = 0; q + 1 < grp_ptr.size(); ++q) grp_max = std::max(grp_max, grp_ptr[q + 1] - grp_ptr[q]);
 }

@@ -601,6 +601,10 @@ static void raise_wait_timeout(ttn_ctx* ctx) {
   if (v == TTN_WAIT_FLAG_SELFTEST)
     TTN_FAIL(TTN_ETIMEOUT, "bounded-wait self-test: the barrier wait gave up as intended (no "
                            "copy was in flight; the context stays usable)");
+  if (v == TTN_WAIT_FLAG_MMA)
+    TTN_FAIL(TTN_ETIMEOUT, "a wait for tensor-core MMA completion on the device gave up after "
+                           "2 s; results of the work issued since the previous call are not valid "
+                           "and the context must be destroyed");
   TTN_FAIL(TTN_ETIMEOUT, "a bulk-copy barrier wait on the device gave up after 2 s; copies may "
                          "still have been landing when the waiting block left, so results of the "
                          "work issued since the previous call are not valid and the context must "

@@ -37,7 +37,7 @@ std::string ttn_fmt(const char* f, ...);
 
 // Values of the context's wait flag: a bulk-copy kernel gave up waiting (copies may still have
 // been landing when its CTA left), or the bounded-wait self-test ran out (nothing in flight).
-enum : unsigned { TTN_WAIT_FLAG_COPY = 1u, TTN_WAIT_FLAG_SELFTEST = 2u };
+enum : unsigned { TTN_WAIT_FLAG_COPY = 1u, TTN_WAIT_FLAG_SELFTEST = 2u, TTN_WAIT_FLAG_MMA = 3u };
 
 // ------------------------------------------------------------------------------------------------
 // tree
@@ -214,6 +214,7 @@ struct StageHost {
   bool single = true;               // every item has exactly one segment
   bool a4 = true, b4 = true;        // every A / B offset a multiple of 4 elements
   bool c2 = true;                   // every C offset even
+  bool c4 = true;                   // every C offset a multiple of 4 elements
   int grp_max = 0;                  // largest A group
   void finalize();
 };

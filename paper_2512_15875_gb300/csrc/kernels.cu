@@ -2,7 +2,9 @@
 // segment sums (the workhorse of every node contraction), tensor permutes, per-pair dots.
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <set>
 
 #include "internal.h"
@@ -779,8 +781,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 // Waits for phase `parity` of the barrier; gives up after budget_ns of device time (2 s for
 // the bulk-copy kernels), writes flag_value into the context's wait flag and returns false (the
-// caller then leaves the CTA without touching the staged data).
+// caller then leaves the CTA without touching the staged data). A wait that has already lasted
+// 1 ms also gives up, without writing, once another CTA has set the flag, so that a launch whose
+// waits cannot complete ends after one budget instead of one budget per CTA.
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
+constexpr unsigned long long kWaitPeerCheckNs = 1000000ull;
+// second, short wait for work still in flight after a wait gave up
+constexpr unsigned long long kWaitDrainNs = 10000000ull;
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
                                           unsigned* flag,
                                           unsigned long long budget_ns = kWaitBudgetNs,
@@ -799,6 +806,9 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
       const unsigned long long now = global_ns();
       if (t0 == 0) {
         t0 = now;
+      } else if (flag && now - t0 > kWaitPeerCheckNs &&
+                 *reinterpret_cast<volatile unsigned*>(flag) != 0u) {
+        return false;
       } else if (now - t0 > budget_ns) {
         if (flag) {
           *reinterpret_cast<volatile unsigned*>(flag) = flag_value;
@@ -1262,6 +1272,241 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
                       nrow, g.N, acc, vec_store);
 }
 
+// ---- level stage on the fifth-generation tensor cores (tcgen05.mma, tensor-memory accumulators)
+// The grouped level stage C_j[r][a] = sum_b A[b][r] E_j[a][b] of one A group (the items j that
+// read the same A slice, i.e. the children of one prefix in the TTNO trie) for a 128-row tile:
+//  * the A tile (K slices of up to 128 contiguous rows) arrives by bulk copies; the group's
+//    environment slices are read with plain loads while those copies are in flight;
+//  * both operands are split x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) into the K-major,
+//    non-swizzled layout the shared-memory matrix descriptors address: core matrices of 8 rows x
+//    16 bytes, K-adjacent core matrices 128 bytes apart (leading byte offset), consecutive 8-row
+//    groups 32 * Kp bytes apart (stride byte offset), Kp = K rounded up to 8 with zero padding;
+//  * one thread issues tcgen05.mma kind::tf32 (M = 128, N = items x NA rounded up to 16, K = 8
+//    per instruction), lo*hi + hi*lo + hi*hi per K step, float32 accumulation in tensor memory
+//    (the 3xTF32 product, ~2^-21 relative per product); a group with more items than fit in
+//    kUmmaCols accumulator columns runs in several passes;
+//  * warp w reads tensor-memory lanes 32w..32w+31 (= rows) back with tcgen05.ld and stores them.
+// Every wait is bounded (2 s); after a timeout the CTA waits once more, then frees its tensor
+// memory and leaves, and the host reports TTN_ETIMEOUT.
+constexpr int kUmmaRows = 128;   // MMA M: one accumulator lane per row
+constexpr int kUmmaCols = 128;   // tensor-memory columns allocated per CTA (<= 4 CTAs per SM)
+
+// shared-memory matrix descriptor: start address, leading byte offset 128, stride byte offset,
+// descriptor version 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned addr, unsigned sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// instruction descriptor of kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(unsigned d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          int accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrives once on the barrier when every MMA this thread issued so far has completed
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 8 consecutive float32 columns of this thread's tensor-memory lane (the warp's 32 lanes)
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+// hi / lo parts of 4 K-consecutive values of row n into the canonical K-major layout
+__device__ __forceinline__ void umma_store_split(uint32_t* hi, uint32_t* lo, int n, int kq, int kp,
+                                                 const float* x) {
+  const int off = (n & 7) * 4 + (n >> 3) * 8 * kp + kq * 32;
+  uint4 h, l;
+  h.x = tf32_bits(x[0]);
+  h.y = tf32_bits(x[1]);
+  h.z = tf32_bits(x[2]);
+  h.w = tf32_bits(x[3]);
+  l.x = tf32_bits(x[0] - __uint_as_float(h.x));
+  l.y = tf32_bits(x[1] - __uint_as_float(h.y));
+  l.z = tf32_bits(x[2] - __uint_as_float(h.z));
+  l.w = tf32_bits(x[3] - __uint_as_float(h.w));
+  *reinterpret_cast<uint4*>(hi + off) = h;
+  *reinterpret_cast<uint4*>(lo + off) = l;
+}
+
+// Shared memory of one CTA (bytes): raw A tile, A hi/lo, B hi/lo for nb_rows rows.
+__host__ __device__ inline size_t umma_level_smem(int K, int kp, int nb_rows) {
+  return 4 * ((size_t)K * kUmmaRows + 2 * (size_t)kUmmaRows * kp + 2 * (size_t)nb_rows * kp);
+}
+
+template <int NA>
+__global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles, int kp,
+                                                         int nb_rows, int et, int vec4) {
+  extern __shared__ __align__(128) unsigned char usm[];
+  __shared__ __align__(8) unsigned long long bar_ld;
+  __shared__ __align__(8) unsigned long long bar_mma;
+  __shared__ unsigned tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const long long bid = blockIdx.x;
+  const int rt = (int)(bid % rtiles);
+  const long long rest = bid / rtiles;
+  const int q = (int)(rest % g.st.n_grp);
+  const int pair = (int)(rest / g.st.n_grp);
+  const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
+  const int r0 = rt * kUmmaRows;
+  const int nrow = min(kUmmaRows, g.M - r0);
+  const int K = g.K, N = g.N;
+  const unsigned sbo = 32u * (unsigned)kp;
+  float* As = reinterpret_cast<float*>(usm);
+  uint32_t* Ah = reinterpret_cast<uint32_t*>(usm + (size_t)K * kUmmaRows * 4);
+  uint32_t* Al = Ah + kUmmaRows * kp;
+  uint32_t* Bh = Al + kUmmaRows * kp;
+  uint32_t* Bl = Bh + nb_rows * kp;
+  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
+  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+
+  if (tid == 0) {
+    mbar_init(&bar_ld, 1);
+    mbar_init(&bar_mma, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kUmmaCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  if (tid == 0) {
+    const float* Ab = Abase + g.st.grp_a[q] + r0;
+    mbar_expect_tx(&bar_ld, (unsigned)(K * nrow) * 4u);
+    for (int b = 0; b < K; ++b)
+      bulk_copy_g2s(As + b * kUmmaRows, Ab + (long long)b * g.a_sk, nrow * 4u, &bar_ld);
+  }
+  // B operand: row n = j * NA + a of the group's slices (rows past the items are zero)
+  const int kq4 = kp >> 2;
+  for (int i = tid; i < nb_rows * kq4; i += kUmmaRows) {
+    const int n = i / kq4, kq = i - n * kq4;
+    const int j = n / NA, a = n - j * NA;
+    float x[4] = {0.f, 0.f, 0.f, 0.f};
+    if (j < ns && a < N) {
+      const float* Ej = Bbase + g.st.grp_b[gs + j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = 4 * kq + u;
+        if (b < K) x[u] = et ? Ej[(long long)b * N + a] : Ej[(long long)a * K + b];
+      }
+    }
+    umma_store_split(Bh, Bl, n, kq, kp, x);
+  }
+  const bool ok = !__syncthreads_or(!mbar_wait(&bar_ld, 0, g.wait_flag));
+  if (ok) {
+    // A operand: thread = row (rows past the tile and columns past K are zero)
+    for (int kq = 0; kq < kq4; ++kq) {
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = 4 * kq + u;
+        x[u] = (tid < nrow && b < K) ? As[b * kUmmaRows + tid] : 0.f;
+      }
+      umma_store_split(Ah, Al, tid, kq, kp, x);
+    }
+  }
+  fence_proxy_async();   // the operands written above become visible to the tensor cores
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  bool ok_mma = ok;
+  unsigned phase = 0;
+  if (ok) {
+    long long cidx = 0;
+    if (g.c_mode == MODE_PAIR) cidx = pair;
+    else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+    else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+    float* Cpair = static_cast<float*>(g.C) + cidx * g.c_pstride;
+    const unsigned a_hi = smem_addr(Ah), a_lo = smem_addr(Al);
+    const unsigned b_hi = smem_addr(Bh), b_lo = smem_addr(Bl);
+    constexpr int ipp = kUmmaCols / NA;   // items per pass
+    for (int j0 = 0; j0 < ns; j0 += ipp) {
+      const int nj = min(ipp, ns - j0);
+      if (tid == 0) {
+        const uint32_t idesc = umma_idesc_tf32(kUmmaRows, (nj * NA + 15) & ~15);
+        const unsigned boff = (unsigned)(j0 * NA / 8) * sbo;
+        for (int ks = 0; ks < kp / 8; ++ks) {
+          const unsigned ko = (unsigned)ks * 256u;   // two core matrices along K
+          umma_tf32(tmem, umma_sdesc(a_lo + ko, sbo), umma_sdesc(b_hi + boff + ko, sbo), idesc,
+                    ks > 0);
+          umma_tf32(tmem, umma_sdesc(a_hi + ko, sbo), umma_sdesc(b_lo + boff + ko, sbo), idesc, 1);
+          umma_tf32(tmem, umma_sdesc(a_hi + ko, sbo), umma_sdesc(b_hi + boff + ko, sbo), idesc, 1);
+        }
+        umma_commit(&bar_mma);
+      }
+      ok_mma = !__syncthreads_or(
+          !mbar_wait(&bar_mma, phase, g.wait_flag, kWaitBudgetNs, TTN_WAIT_FLAG_MMA));
+      if (!ok_mma) break;
+      phase ^= 1u;
+      tc_fence_after();
+      const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
+      for (int jj = 0; jj < nj; ++jj) {
+        float v[NA];
+#pragma unroll
+        for (int c = 0; c < NA; c += 8) tmem_ld8(lane_base + (unsigned)(jj * NA + c), v + c);
+        if (tid < nrow) {
+          float* o = Cpair + g.st.grp_c[gs + j0 + jj] + (long long)(r0 + tid) * N;
+          if (vec4) {
+#pragma unroll
+            for (int c = 0; c < NA; c += 4)
+              *reinterpret_cast<float4*>(o + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < NA; ++c)
+              if (c < N) o[c] = v[c];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+    }
+  }
+  // leave only with nothing in flight that targets this CTA (bounded second waits)
+  if (!ok) mbar_wait(&bar_ld, 0, nullptr, kWaitDrainNs);
+  if (ok && !ok_mma) mbar_wait(&bar_mma, phase, nullptr, kWaitDrainNs);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kUmmaCols)
+                 : "memory");
+  }
+}
+
 namespace {
 int level_tma_na(int N) { return N <= 8 ? 8 : N <= 16 ? 16 : N <= 24 ? 24 : N <= 32 ? 32 : 0; }
 int level_tma_rows(int M) {
@@ -1308,6 +1553,75 @@ static bool level_tma_ok(const GemmDesc& g) {
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
     return false;
   return g.hst->a4 && g.hst->b4;
+}
+
+// The tensor-core grouped level stage takes A-group launches the bulk-copy kernel takes, with
+// N <= 32 and K <= 64 (any K: the padding to a multiple of 8 is zero).
+static bool umma_level_ok(const GemmDesc& g) {
+  if (g.st.n_grp <= 0 || g.K > 64 || level_tma_na(g.N) == 0 || !level_tma_ok(g)) return false;
+  const int kp = (g.K + 7) & ~7;
+  return umma_level_smem(g.K, kp, g.hst->grp_max * level_tma_na(g.N) + 8) <= 220 * 1024;
+}
+
+// Dynamic shared memory for a launch of `kern` with `need` bytes, padded until at most
+// 512 / kUmmaCols CTAs fit on an SM, so that every CTA's tcgen05.alloc finds free columns.
+static size_t umma_launch_smem(const void* kern, size_t need, int device) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, size_t, int>, size_t> memo;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_tuple(kern, need, device);
+  auto it = memo.find(key);
+  if (it != memo.end()) return it->second;
+  int optin = 0;
+  CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  cudaFuncAttributes fa{};
+  CUDA_CHECK(cudaFuncGetAttributes(&fa, kern));
+  const size_t dyn_max = (size_t)optin - fa.sharedSizeBytes;
+  TTN_REQUIRE(need <= dyn_max, "tensor-core level kernel: %zu bytes of shared memory needed",
+              need);
+  CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
+  size_t sm = need;
+  for (;;) {
+    int resident = 0;
+    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kUmmaRows, sm));
+    TTN_REQUIRE(resident >= 1, "tensor-core level kernel: does not fit on an SM");
+    if (resident * kUmmaCols <= 512) break;
+    sm += 4096;
+    TTN_REQUIRE(sm <= dyn_max, "tensor-core level kernel: cannot bound CTAs per SM");
+  }
+  memo[key] = sm;
+  return sm;
+}
+
+static void launch_level_umma(ttn_ctx* ctx, const GemmDesc& g) {
+  const int na = level_tma_na(g.N);
+  const int kp = (g.K + 7) & ~7;
+  const int nb_rows = g.hst->grp_max * na + 8;
+  const size_t need = umma_level_smem(g.K, kp, nb_rows);
+  const int rt = (g.M + kUmmaRows - 1) / kUmmaRows;
+  const long long grid = (long long)rt * g.st.n_grp * g.n_pairs;
+  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
+  const bool vec4 = g.N == na && g.N % 4 == 0 && g.c_pstride % 4 == 0 &&
+                    reinterpret_cast<uintptr_t>(g.C) % 16 == 0 && g.hst->c4;
+  const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
+  const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
+  static const char* nm[] = {"level_umma_tf32x3_8", "level_umma_tf32x3_16",
+                             "level_umma_tf32x3_24", "level_umma_tf32x3_32"};
+  LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(float)));
+  GemmDesc gd = g;
+  gd.wait_flag = ctx->d_wait;
+  auto go = [&](auto kern) {
+    const size_t sm = umma_launch_smem((const void*)kern, need, ctx->device);
+    kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, nb_rows, et ? 1 : 0,
+                                                         vec4 ? 1 : 0);
+  };
+  switch (na) {
+    case 8: go(level_umma_kernel<8>); break;
+    case 16: go(level_umma_kernel<16>); break;
+    case 24: go(level_umma_kernel<24>); break;
+    default: go(level_umma_kernel<32>); break;
+  }
+  CUDA_LAUNCH_CHECK();
 }
 
 template <class T>
@@ -1390,6 +1704,10 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
       }
     }
     CUDA_LAUNCH_CHECK();
+    return;
+  }
+  if (sizeof(T) == 4 && ctx->tf32x3 && umma_level_ok(g)) {
+    launch_level_umma(ctx, g);
     return;
   }
   if (sizeof(T) == 4 && level_tma_ok(g)) {
