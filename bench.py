@@ -58,7 +58,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ttn", choices=["ttn", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "fp64"])
+    ap.add_argument("--precision", default="fp32",
+                    choices=["fp32", "tf32x3", "tf32x3_tc05", "fp64"])
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--block", type=int, default=0,
                     help="states in the LOBPCG block (default: wanted + 16 guard vectors)")
@@ -259,7 +260,7 @@ def roofline_of(prof, mp):
     sec = rec["ms"] / 1e3
     if "f64" in name or name.startswith("jacobi"):
         bound, peak, src = "alu", mp["fp64_tflops"], mp["fp64_src"]
-    elif "tf32x3" in name:
+    elif "tf32x3" in name or "tc05" in name:
         bound, peak, src = "tensor", mp["tf32x3_tflops"], mp["tf32x3_src"]
     else:
         bound, peak, src = "alu", mp["fp32_tflops"], mp["fp32_src"]
@@ -720,6 +721,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": out["t"] * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32x3": "f32 (tf32x3 tensor-core levels)",
+                  "tf32x3_tc05": "f32 (tf32x3 levels on tcgen05)",
                   "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w.description}, the lowest {nw} states",
                    "block": nb, "guard_vectors": nb - nw, "subspace": 3 * nb,

@@ -48,9 +48,12 @@ typedef enum {
   TTN_FP64 = 0,   /* every contraction in float64 */
   TTN_FP32 = 1,   /* node contractions in float32 with float32 accumulation; Gram closure,
                      Lanczos/MINRES scalars and Rayleigh-Ritz in float64 */
-  TTN_TF32X3 = 2  /* as TTN_FP32, but the level stages of the node contractions run on the
+  TTN_TF32X3 = 2, /* as TTN_FP32, but the level stages of the node contractions run on the
                      tensor cores as TF32 products with the 3xTF32 split (x = hi + lo, three
-                     products per term) and float32 accumulation */
+                     products per term) and float32 accumulation (mma.sync kernels) */
+  TTN_TF32X3_TC05 = 3 /* as TTN_TF32X3, with the level stages on the fifth-generation tensor
+                         cores: tcgen05.mma kind::tf32 from shared-memory operand descriptors
+                         into float32 accumulators in tensor memory */
 } ttn_precision;
 
 #define TTN_MAX_LEGS 8   /* stride of per-entry w-tuples in the TTNO entry arrays */

@@ -54,7 +54,7 @@ extern "C" ttn_status ttn_apply_block(ttn_ctx* ctx, const ttn_ttno* Hc, const tt
   try {
     ttn_ttno* H = const_cast<ttn_ttno*>(Hc);
     TTN_REQUIRE(H->tree.same_shape(in->tree), "TTNO and block live on different trees");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     const TreeInfo& tr = in->tree;
     std::vector<int> nb(tr.n);
     for (int i = 0; i < tr.n; ++i) nb[i] = H->wbond[i] * in->bond[i];

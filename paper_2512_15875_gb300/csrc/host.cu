@@ -689,6 +689,7 @@ ttn_status ttn_create(ttn_ctx** out, int device, void* cuda_stream) {
     TTN_REQUIRE(device >= 0 && device < n, "device %d not present (%d devices)", device, n);
     CUDA_CHECK(cudaSetDevice(device));
     ctx->device = device;
+    CUDA_CHECK(cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device));
     if (cuda_stream) {
       ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1049,7 +1050,7 @@ ttn_status ttn_env_update(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra
     check_pair_blocks(Hc, bra, ket);
     TTN_REQUIRE(envs->tree.same_shape(bra->tree), "envs created for another tree");
     TTN_REQUIRE(direction >= 0 && direction <= 2, "direction must be 0, 1 or 2");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision %d", (int)prec);
+    TTN_REQUIRE(valid_precision(prec), "unknown precision %d", (int)prec);
     TTN_REQUIRE(n_pairs >= 0 && (n_pairs == 0 || (pair_bra && pair_ket)), "pairs");
     for (int i = 0; i < n_pairs; ++i)
       TTN_REQUIRE(pair_bra[i] >= 0 && pair_bra[i] < bra->n_states && pair_ket[i] >= 0 &&
@@ -1284,7 +1285,7 @@ ttn_status ttn_gram(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* bra, cons
     check_pair_blocks(Hc, bra, ket);
     TTN_REQUIRE(bra->bond == ket->bond || bra != ket, "internal");
     TTN_REQUIRE(ld >= ket->n_states, "ld < number of ket states");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision %d", (int)prec);
+    TTN_REQUIRE(valid_precision(prec), "unknown precision %d", (int)prec);
     const size_t mat = (size_t)bra->n_states * ld;
     unsigned bad = 0;
     auto one = [&](ttn_ttno* H, double* out) {

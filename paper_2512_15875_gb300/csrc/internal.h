@@ -95,6 +95,7 @@ struct LaunchRecord {
 };
 struct ttn_ctx {
   int device = 0;
+  int sm_count = 0;   // streaming multiprocessors of the device (persistent grids)
   cudaStream_t stream = 0;
   bool own_stream = false;
   std::string last_error;
@@ -105,6 +106,7 @@ struct ttn_ctx {
   std::vector<cudaEvent_t> event_pool;
   double flops_total = 0.0;      // algorithmic flops of every GEMM launched (always counted)
   bool tf32x3 = false;           // float32 calls route level stages to tensor cores
+  bool tc05 = false;             // ... and those stages to the tcgen05 kernels
   bool capturing = false;        // a CUDA graph is being captured on the stream (no events)
   // Set (host-mapped) by a kernel whose bounded wait on a barrier gave up (TTN_WAIT_FLAG_*);
   // read and cleared by the next entry point, which then returns TTN_ETIMEOUT.
@@ -124,15 +126,22 @@ struct ttn_ctx {
 void iter_clock_start(ttn_ctx* ctx);
 void iter_clock_mark(ttn_ctx* ctx);
 
-// Sets ctx->tf32x3 for the duration of one entry-point call.
+// Sets ctx->tf32x3 / ctx->tc05 for the duration of one entry-point call.
 struct PrecisionScope {
   ttn_ctx* ctx;
-  bool saved;
-  PrecisionScope(ttn_ctx* c, int prec) : ctx(c), saved(c->tf32x3) {
-    ctx->tf32x3 = prec == TTN_TF32X3;
+  bool saved, saved_tc05;
+  PrecisionScope(ttn_ctx* c, int prec) : ctx(c), saved(c->tf32x3), saved_tc05(c->tc05) {
+    ctx->tf32x3 = prec == TTN_TF32X3 || prec == TTN_TF32X3_TC05;
+    ctx->tc05 = prec == TTN_TF32X3_TC05;
   }
-  ~PrecisionScope() { ctx->tf32x3 = saved; }
+  ~PrecisionScope() {
+    ctx->tf32x3 = saved;
+    ctx->tc05 = saved_tc05;
+  }
 };
+inline bool valid_precision(int prec) {
+  return prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3 || prec == TTN_TF32X3_TC05;
+}
 // float64 for TTN_FP64, float32 otherwise
 inline bool is_fp64(int prec) { return prec == TTN_FP64; }
 

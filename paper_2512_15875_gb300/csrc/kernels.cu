@@ -1284,12 +1284,11 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
 //  * one thread issues tcgen05.mma kind::tf32 (M = 128, N = items x NA rounded up to 16, K = 8
 //    per instruction), lo*hi + hi*lo + hi*hi per K step, float32 accumulation in tensor memory
 //    (the 3xTF32 product, ~2^-21 relative per product); a group with more items than fit in
-//    kUmmaCols accumulator columns runs in several passes;
+//    the CTA's accumulator columns (at most 128) runs in several passes;
 //  * warp w reads tensor-memory lanes 32w..32w+31 (= rows) back with tcgen05.ld and stores them.
 // Every wait is bounded (2 s); after a timeout the CTA waits once more, then frees its tensor
 // memory and leaves, and the host reports TTN_ETIMEOUT.
 constexpr int kUmmaRows = 128;   // MMA M: one accumulator lane per row
-constexpr int kUmmaCols = 128;   // tensor-memory columns allocated per CTA (<= 4 CTAs per SM)
 
 // shared-memory matrix descriptor: start address, leading byte offset 128, stride byte offset,
 // descriptor version 1 (bits 46-47), base offset 0, no swizzle (bits 61-63 = 0)
@@ -1323,19 +1322,110 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// 8 consecutive float32 columns of this thread's tensor-memory lane (the warp's 32 lanes)
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float* v) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
-      "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr)
-      : "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+// shared -> global bulk copy (both addresses 16-byte aligned, bytes a multiple of 16), tracked
+// by this thread's bulk groups
+__device__ __forceinline__ void bulk_store_s2g(void* dst, const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
+// waits until at most one of this thread's bulk stores still reads its shared-memory source
+__device__ __forceinline__ void bulk_store_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// NA consecutive float32 columns of this thread's lane: the loads of one row and a single
+// wait in one asm statement (the destination registers are not valid before the wait)
+template <int NA>
+__device__ __forceinline__ void tmem_ld_row(unsigned taddr, float* v) {
+  uint32_t r[NA];
+  if constexpr (NA == 8) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+  } else if constexpr (NA == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+  } else if constexpr (NA == 24) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%25];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(taddr), "r"(taddr + 16u)
+        : "memory");
+  } else {
+    static_assert(NA == 32, "row width");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+  }
+#pragma unroll
+  for (int i = 0; i < NA; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Epilogue of one 128 x N tile, warp by warp (no CTA barrier): warp w's 32 rows (v = this
+// thread's row) go to its own staging tile (two per warp, alternating) and out with one bulk
+// store issued by the warp's first lane, or with direct stores when bulk_out is 0. `n_out`
+// counts the warp's bulk stores (its first lane's bulk groups).
+template <int NA>
+__device__ __forceinline__ void umma_store_tile(float* o, int nrow, int N, const float* v,
+                                                float* stage_warp, int& n_out, int bulk_out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nr = min(32, nrow - warp * 32);
+  if (nr <= 0) return;
+  float* ow = o + (long long)warp * 32 * N;
+  if (bulk_out) {
+    float* st = stage_warp + (n_out & 1) * 32 * N;
+    if (lane == 0) bulk_store_wait_read1();   // the store that last read this tile is done
+    __syncwarp();
+    if (lane < nr) {
+#pragma unroll
+      for (int c = 0; c < NA; c += 4)
+        if (c < N)
+          *reinterpret_cast<float4*>(st + lane * N + c) =
+              make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+    }
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) bulk_store_s2g(ow, st, (unsigned)(nr * N) * 4u);
+    ++n_out;
+  } else if (lane < nr) {
+#pragma unroll
+    for (int c = 0; c < NA; ++c)
+      if (c < N) ow[(long long)lane * N + c] = v[c];
+  }
+}
+
 // hi / lo parts of 4 K-consecutive values of row n into the canonical K-major layout
 __device__ __forceinline__ void umma_store_split(uint32_t* hi, uint32_t* lo, int n, int kq, int kp,
                                                  const float* x) {
@@ -1353,36 +1443,54 @@ __device__ __forceinline__ void umma_store_split(uint32_t* hi, uint32_t* lo, int
   *reinterpret_cast<uint4*>(lo + off) = l;
 }
 
-// Shared memory of one CTA (bytes): raw A tile, A hi/lo, B hi/lo for nb_rows rows.
-__host__ __device__ inline size_t umma_level_smem(int K, int kp, int nb_rows) {
-  return 4 * ((size_t)K * kUmmaRows + 2 * (size_t)kUmmaRows * kp + 2 * (size_t)nb_rows * kp);
+// Shared-memory plan of one CTA (byte offsets, each region 128-byte aligned).
+struct UmmaLevelSmem {
+  size_t raw_a, raw_e, a_hi, a_lo, b_hi, b_lo, stage, total;
+};
+__host__ __device__ inline size_t umma_align(size_t x) { return (x + 127) & ~(size_t)127; }
+__host__ __device__ inline UmmaLevelSmem umma_level_plan(int K, int kp, int N, int sb_max,
+                                                         int nb_rows) {
+  UmmaLevelSmem p;
+  const size_t nk4 = (size_t)((N * K + 3) & ~3);
+  p.raw_a = 0;
+  p.raw_e = umma_align(p.raw_a + 4 * (size_t)K * kUmmaRows);
+  p.a_hi = umma_align(p.raw_e + 4 * (size_t)sb_max * nk4);
+  p.a_lo = umma_align(p.a_hi + 4 * (size_t)kUmmaRows * kp);
+  p.b_hi = umma_align(p.a_lo + 4 * (size_t)kUmmaRows * kp);
+  p.b_lo = umma_align(p.b_hi + 4 * (size_t)nb_rows * kp);
+  p.stage = umma_align(p.b_lo + 4 * (size_t)nb_rows * kp);
+  p.total = umma_align(p.stage + 2 * 4 * (size_t)kUmmaRows * N);
+  return p;
 }
 
+// Persistent CTAs walk the work list (pair, A group, 128-row tile) with a stride of the grid.
+// Per work item: the A tile and the group's slices arrive by bulk copies on bar_ld (requested
+// while the previous item was being finished), are split into the operand buffers, the raw
+// buffers are refilled for the next item at once, one thread issues the MMAs (one pass of up to
+// `ncols` accumulator columns at a time), and each item's 128 x N result goes from tensor memory
+// through one of two staging tiles to global memory by a bulk store (direct stores when the
+// output is not 16-byte aligned).
 template <int NA>
 __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles, int kp,
-                                                         int nb_rows, int et, int vec4) {
+                                                         int sb_max, int nb_rows, int ncols,
+                                                         int et, int bulk_out,
+                                                         long long n_work) {
   extern __shared__ __align__(128) unsigned char usm[];
   __shared__ __align__(8) unsigned long long bar_ld;
   __shared__ __align__(8) unsigned long long bar_mma;
   __shared__ unsigned tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const long long bid = blockIdx.x;
-  const int rt = (int)(bid % rtiles);
-  const long long rest = bid / rtiles;
-  const int q = (int)(rest % g.st.n_grp);
-  const int pair = (int)(rest / g.st.n_grp);
-  const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
-  const int r0 = rt * kUmmaRows;
-  const int nrow = min(kUmmaRows, g.M - r0);
   const int K = g.K, N = g.N;
   const unsigned sbo = 32u * (unsigned)kp;
-  float* As = reinterpret_cast<float*>(usm);
-  uint32_t* Ah = reinterpret_cast<uint32_t*>(usm + (size_t)K * kUmmaRows * 4);
-  uint32_t* Al = Ah + kUmmaRows * kp;
-  uint32_t* Bh = Al + kUmmaRows * kp;
-  uint32_t* Bl = Bh + nb_rows * kp;
-  const float* Abase = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket);
-  const float* Bbase = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+  const int nk4 = (N * K + 3) & ~3;
+  const UmmaLevelSmem L = umma_level_plan(K, kp, N, sb_max, nb_rows);
+  float* As = reinterpret_cast<float*>(usm + L.raw_a);
+  float* Er = reinterpret_cast<float*>(usm + L.raw_e);
+  uint32_t* Ah = reinterpret_cast<uint32_t*>(usm + L.a_hi);
+  uint32_t* Al = reinterpret_cast<uint32_t*>(usm + L.a_lo);
+  uint32_t* Bh = reinterpret_cast<uint32_t*>(usm + L.b_hi);
+  uint32_t* Bl = reinterpret_cast<uint32_t*>(usm + L.b_lo);
+  float* stage = reinterpret_cast<float*>(usm + L.stage);
 
   if (tid == 0) {
     mbar_init(&bar_ld, 1);
@@ -1392,7 +1500,7 @@ __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles,
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&tmem_slot)),
-                 "r"(kUmmaCols)
+                 "r"(ncols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -1401,31 +1509,47 @@ __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles,
   tc_fence_after();
   const unsigned tmem = tmem_slot;
 
-  if (tid == 0) {
-    const float* Ab = Abase + g.st.grp_a[q] + r0;
-    mbar_expect_tx(&bar_ld, (unsigned)(K * nrow) * 4u);
+  // work item -> (pair, group, row tile)
+  auto decode = [&](long long w, int& pair, int& q, int& r0, int& nrow) {
+    const int rt = (int)(w % rtiles);
+    const long long rest = w / rtiles;
+    q = (int)(rest % g.st.n_grp);
+    pair = (int)(rest / g.st.n_grp);
+    r0 = rt * kUmmaRows;
+    nrow = min(kUmmaRows, g.M - r0);
+  };
+  auto request = [&](long long w) {   // thread 0: bulk copies of work item w
+    int pair, q, r0, nrow;
+    decode(w, pair, q, r0, nrow);
+    const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
+    const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.grp_a[q] + r0;
+    const float* Bb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
+    mbar_expect_tx(&bar_ld, (unsigned)(K * nrow + ns * N * K) * 4u);
     for (int b = 0; b < K; ++b)
       bulk_copy_g2s(As + b * kUmmaRows, Ab + (long long)b * g.a_sk, nrow * 4u, &bar_ld);
-  }
-  // B operand: row n = j * NA + a of the group's slices (rows past the items are zero)
+    for (int j = 0; j < ns; ++j)
+      bulk_copy_g2s(Er + j * nk4, Bb + g.st.grp_b[gs + j], N * K * 4u, &bar_ld);
+  };
+
+  long long w = blockIdx.x;
+  if (tid == 0 && w < n_work) request(w);
+  unsigned ph_ld = 0, ph_mma = 0;
+  bool ld_pending = w < n_work, mma_pending = false, failed = false;
+  int n_stores = 0;   // bulk stores of this warp (its staging tile = n_stores % 2)
+  const unsigned a_hi = smem_addr(Ah), a_lo = smem_addr(Al);
+  const unsigned b_hi = smem_addr(Bh), b_lo = smem_addr(Bl);
   const int kq4 = kp >> 2;
-  for (int i = tid; i < nb_rows * kq4; i += kUmmaRows) {
-    const int n = i / kq4, kq = i - n * kq4;
-    const int j = n / NA, a = n - j * NA;
-    float x[4] = {0.f, 0.f, 0.f, 0.f};
-    if (j < ns && a < N) {
-      const float* Ej = Bbase + g.st.grp_b[gs + j];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int b = 4 * kq + u;
-        if (b < K) x[u] = et ? Ej[(long long)b * N + a] : Ej[(long long)a * K + b];
-      }
+  for (; w < n_work; w += gridDim.x) {
+    int pair, q, r0, nrow;
+    decode(w, pair, q, r0, nrow);
+    const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
+    if (__syncthreads_or(!mbar_wait(&bar_ld, ph_ld, g.wait_flag))) {
+      failed = true;
+      break;
     }
-    umma_store_split(Bh, Bl, n, kq, kp, x);
-  }
-  const bool ok = !__syncthreads_or(!mbar_wait(&bar_ld, 0, g.wait_flag));
-  if (ok) {
-    // A operand: thread = row (rows past the tile and columns past K are zero)
+    ph_ld ^= 1u;
+    ld_pending = false;
+    // split into the operand buffers (rows / columns past the data are zero)
     for (int kq = 0; kq < kq4; ++kq) {
       float x[4];
 #pragma unroll
@@ -1435,23 +1559,37 @@ __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles,
       }
       umma_store_split(Ah, Al, tid, kq, kp, x);
     }
-  }
-  fence_proxy_async();   // the operands written above become visible to the tensor cores
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
+    for (int i = tid; i < nb_rows * kq4; i += kUmmaRows) {
+      const int n = i / kq4, kq = i - n * kq4;
+      const int j = n / NA, a = n - j * NA;
+      float x[4] = {0.f, 0.f, 0.f, 0.f};
+      if (j < ns && a < N) {
+        const float* Ej = Er + j * nk4;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int b = 4 * kq + u;
+          if (b < K) x[u] = et ? Ej[b * N + a] : Ej[a * K + b];
+        }
+      }
+      umma_store_split(Bh, Bl, n, kq, kp, x);
+    }
+    fence_proxy_async();   // operands visible to the tensor cores
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const long long wn = w + gridDim.x;
+    if (tid == 0 && wn < n_work) {
+      fence_proxy_async();   // raw buffers were read above; refill them for the next item
+      request(wn);
+    }
+    ld_pending = wn < n_work;
 
-  bool ok_mma = ok;
-  unsigned phase = 0;
-  if (ok) {
     long long cidx = 0;
     if (g.c_mode == MODE_PAIR) cidx = pair;
     else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
     else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
     float* Cpair = static_cast<float*>(g.C) + cidx * g.c_pstride;
-    const unsigned a_hi = smem_addr(Ah), a_lo = smem_addr(Al);
-    const unsigned b_hi = smem_addr(Bh), b_lo = smem_addr(Bl);
-    constexpr int ipp = kUmmaCols / NA;   // items per pass
+    const int ipp = ncols / NA;
     for (int j0 = 0; j0 < ns; j0 += ipp) {
       const int nj = min(ipp, ns - j0);
       if (tid == 0) {
@@ -1466,43 +1604,256 @@ __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles,
         }
         umma_commit(&bar_mma);
       }
-      ok_mma = !__syncthreads_or(
-          !mbar_wait(&bar_mma, phase, g.wait_flag, kWaitBudgetNs, TTN_WAIT_FLAG_MMA));
-      if (!ok_mma) break;
-      phase ^= 1u;
+      mma_pending = true;
+      if (__syncthreads_or(
+              !mbar_wait(&bar_mma, ph_mma, g.wait_flag, kWaitBudgetNs, TTN_WAIT_FLAG_MMA))) {
+        failed = true;
+        break;
+      }
+      ph_mma ^= 1u;
+      mma_pending = false;
       tc_fence_after();
       const unsigned lane_base = tmem + ((unsigned)(warp * 32) << 16);
       for (int jj = 0; jj < nj; ++jj) {
         float v[NA];
-#pragma unroll
-        for (int c = 0; c < NA; c += 8) tmem_ld8(lane_base + (unsigned)(jj * NA + c), v + c);
-        if (tid < nrow) {
-          float* o = Cpair + g.st.grp_c[gs + j0 + jj] + (long long)(r0 + tid) * N;
-          if (vec4) {
-#pragma unroll
-            for (int c = 0; c < NA; c += 4)
-              *reinterpret_cast<float4*>(o + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-          } else {
-#pragma unroll
-            for (int c = 0; c < NA; ++c)
-              if (c < N) o[c] = v[c];
-          }
-        }
+        tmem_ld_row<NA>(lane_base + (unsigned)(jj * NA), v);
+        umma_store_tile<NA>(Cpair + g.st.grp_c[gs + j0 + jj] + (long long)r0 * N, nrow, N, v,
+                            stage + warp * 64 * N, n_stores, bulk_out);
       }
       tc_fence_before();
       __syncthreads();
       tc_fence_after();
     }
+    if (failed) break;
   }
   // leave only with nothing in flight that targets this CTA (bounded second waits)
-  if (!ok) mbar_wait(&bar_ld, 0, nullptr, kWaitDrainNs);
-  if (ok && !ok_mma) mbar_wait(&bar_mma, phase, nullptr, kWaitDrainNs);
+  if (failed && ld_pending) mbar_wait(&bar_ld, ph_ld, nullptr, kWaitDrainNs);
+  if (failed && mma_pending) mbar_wait(&bar_mma, ph_mma, nullptr, kWaitDrainNs);
+  if ((tid & 31) == 0) bulk_store_wait_all();
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kUmmaCols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+  }
+}
+
+// Segmented level stage on the tensor cores: Z[item] = sum_seg A_seg x E_seg (the operator-first
+// last level, items = slots, segments = (prefix, slot) groups), one 128-row tile of one item per
+// work item, persistent CTAs striding over the work list. The CTA walks its segments in order
+// through two raw stages (A tile + slice by bulk copies, requested two segments ahead) and two
+// operand buffers (the hi/lo split of a segment is written while the MMAs of the previous one
+// run; a buffer is rewritten only after the MMAs that read it have completed, mma_done[b]). All
+// segments of an item accumulate into one float32 accumulator of roundup16(NA) tensor-memory
+// columns; the finished tile goes out through a staging tile and a bulk store (direct stores
+// when the output is not 16-byte aligned). Items without segments are written as zeros.
+struct UmmaSegSmem {
+  // buffer b of a kind starts at <kind> + b * <kind>_stride
+  size_t raw, raw_stride, op, op_stride, a_lo, b_hi, b_lo;   // a_lo, b_hi, b_lo: within op
+  size_t stage, total;
+};
+__host__ __device__ inline UmmaSegSmem umma_seg_plan(int K, int kp, int N, int nb_rows) {
+  UmmaSegSmem p;
+  const size_t nk4 = (size_t)((N * K + 3) & ~3);
+  p.raw = 0;
+  p.raw_stride = umma_align(4 * ((size_t)K * kUmmaRows + nk4));
+  p.op = 2 * p.raw_stride;
+  p.a_lo = umma_align(4 * (size_t)kUmmaRows * kp);
+  p.b_hi = umma_align(p.a_lo + 4 * (size_t)kUmmaRows * kp);
+  p.b_lo = umma_align(p.b_hi + 4 * (size_t)nb_rows * kp);
+  p.op_stride = umma_align(p.b_lo + 4 * (size_t)nb_rows * kp);
+  p.stage = p.op + 2 * p.op_stride;
+  p.total = umma_align(p.stage + 2 * 4 * (size_t)kUmmaRows * N);
+  return p;
+}
+
+template <int NA>
+__global__ void __launch_bounds__(128) level_umma_seg_kernel(GemmDesc g, int rtiles, int kp,
+                                                             int et, int bulk_out,
+                                                             long long n_work) {
+  constexpr int NB = (NA + 15) & ~15;   // B rows = accumulator columns
+  constexpr int kCols = 32;             // tensor-memory allocation (>= NB, a power of two)
+  static_assert(NB <= kCols, "accumulator wider than its allocation");
+  extern __shared__ __align__(128) unsigned char usm[];
+  __shared__ __align__(8) unsigned long long full[2];
+  __shared__ __align__(8) unsigned long long mma_done[2];
+  __shared__ unsigned tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int K = g.K, N = g.N;
+  const unsigned sbo = 32u * (unsigned)kp;
+  const int nk4 = (N * K + 3) & ~3;
+  const int kq4 = kp >> 2;
+  const UmmaSegSmem L = umma_seg_plan(K, kp, N, NB);
+  float* stage = reinterpret_cast<float*>(usm + L.stage);
+
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full[b], 1);
+      mbar_init(&mma_done[b], 1);
+    }
+    mbar_init_fence();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  auto decode = [&](long long w, int& pair, int& sub, int& r0, int& nrow) {
+    const int rt = (int)(w % rtiles);
+    const long long rest = w / rtiles;
+    sub = (int)(rest % g.st.n_sub);
+    pair = (int)(rest / g.st.n_sub);
+    r0 = rt * kUmmaRows;
+    nrow = min(kUmmaRows, g.M - r0);
+  };
+  auto nseg_of = [&](long long w) {
+    const int sub = (int)((w / rtiles) % g.st.n_sub);
+    return g.st.seg_ptr[sub + 1] - g.st.seg_ptr[sub];
+  };
+  // thread 0's request cursor: the next segment (work item rq_w, segment rq_s) to bulk-copy
+  long long rq_w = blockIdx.x;
+  int rq_s = 0;
+  auto skip_empty = [&]() {
+    while (rq_w < n_work && nseg_of(rq_w) == 0) rq_w += gridDim.x;
+  };
+  auto request = [&](int b) {   // thread 0: copies of the cursor's segment into raw stage b
+    if (rq_w >= n_work) return false;
+    int pair, sub, r0, nrow;
+    decode(rq_w, pair, sub, r0, nrow);
+    const int sg = g.st.seg_ptr[sub] + rq_s;
+    float* As = reinterpret_cast<float*>(usm + L.raw + b * L.raw_stride);
+    float* Es = As + K * kUmmaRows;
+    const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[sg] + r0;
+    const float* Bb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[sg];
+    mbar_expect_tx(&full[b], (unsigned)(K * nrow + N * K) * 4u);
+    for (int kb = 0; kb < K; ++kb)
+      bulk_copy_g2s(As + kb * kUmmaRows, Ab + (long long)kb * g.a_sk, nrow * 4u, &full[b]);
+    bulk_copy_g2s(Es, Bb, N * K * 4u, &full[b]);
+    if (++rq_s == nseg_of(rq_w)) {
+      rq_s = 0;
+      rq_w += gridDim.x;
+      skip_empty();
+    }
+    return true;
+  };
+  int n_req = 0;   // segments requested (thread 0)
+  if (tid == 0) {
+    skip_empty();
+    if (request(0)) ++n_req;
+    if (request(1)) ++n_req;
+  }
+
+  long long t = 0;   // segments consumed by this CTA
+  bool failed = false;
+  int n_stores = 0;   // bulk stores of this warp (its staging tile = n_stores % 2)
+  for (long long w = blockIdx.x; w < n_work && !failed; w += gridDim.x) {
+    int pair, sub, r0, nrow;
+    decode(w, pair, sub, r0, nrow);
+    const int s0 = g.st.seg_ptr[sub], nseg = g.st.seg_ptr[sub + 1] - s0;
+    long long cidx = 0;
+    if (g.c_mode == MODE_PAIR) cidx = pair;
+    else if (g.c_mode == MODE_BRA) cidx = g.pair_bra[pair];
+    else if (g.c_mode == MODE_KET) cidx = g.pair_ket[pair];
+    float* o = static_cast<float*>(g.C) + cidx * g.c_pstride + g.st.sub_c[sub] + (long long)r0 * N;
+    for (int s = 0; s < nseg; ++s, ++t) {
+      const int b = (int)(t & 1);
+      bool ok = mbar_wait(&full[b], (unsigned)((t >> 1) & 1), g.wait_flag);
+      if (ok && t >= 2)
+        ok = mbar_wait(&mma_done[b], (unsigned)(((t >> 1) - 1) & 1), g.wait_flag, kWaitBudgetNs,
+                       TTN_WAIT_FLAG_MMA);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      const float* As = reinterpret_cast<const float*>(usm + L.raw + b * L.raw_stride);
+      const float* Es = As + K * kUmmaRows;
+      unsigned char* op = usm + L.op + b * L.op_stride;
+      uint32_t* Ah = reinterpret_cast<uint32_t*>(op);
+      uint32_t* Al = reinterpret_cast<uint32_t*>(op + L.a_lo);
+      uint32_t* Bh = reinterpret_cast<uint32_t*>(op + L.b_hi);
+      uint32_t* Bl = reinterpret_cast<uint32_t*>(op + L.b_lo);
+      for (int kq = 0; kq < kq4; ++kq) {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int kb = 4 * kq + u;
+          x[u] = (tid < nrow && kb < K) ? As[kb * kUmmaRows + tid] : 0.f;
+        }
+        umma_store_split(Ah, Al, tid, kq, kp, x);
+      }
+      for (int i = tid; i < NB * kq4; i += kUmmaRows) {
+        const int n = i / kq4, kq = i - n * kq4;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (n < N) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int kb = 4 * kq + u;
+            if (kb < K) x[u] = et ? Es[kb * N + n] : Es[n * K + kb];
+          }
+        }
+        umma_store_split(Bh, Bl, n, kq, kp, x);
+      }
+      fence_proxy_async();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        fence_proxy_async();   // raw stage b was read above; refill it two segments ahead
+        if (request(b)) ++n_req;
+        const uint32_t idesc = umma_idesc_tf32(kUmmaRows, NB);
+        const unsigned ah = smem_addr(Ah), al = smem_addr(Al);
+        const unsigned bh = smem_addr(Bh), bl = smem_addr(Bl);
+        for (int ks = 0; ks < kp / 8; ++ks) {
+          const unsigned ko = (unsigned)ks * 256u;
+          umma_tf32(tmem, umma_sdesc(al + ko, sbo), umma_sdesc(bh + ko, sbo), idesc,
+                    (s > 0 || ks > 0) ? 1 : 0);
+          umma_tf32(tmem, umma_sdesc(ah + ko, sbo), umma_sdesc(bl + ko, sbo), idesc, 1);
+          umma_tf32(tmem, umma_sdesc(ah + ko, sbo), umma_sdesc(bh + ko, sbo), idesc, 1);
+        }
+        umma_commit(&mma_done[b]);
+      }
+    }
+    if (failed) break;
+    float v[NA];
+    if (nseg > 0) {
+      const int b = (int)((t - 1) & 1);
+      if (__syncthreads_or(!mbar_wait(&mma_done[b], (unsigned)(((t - 1) >> 1) & 1), g.wait_flag,
+                                      kWaitBudgetNs, TTN_WAIT_FLAG_MMA))) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      tmem_ld_row<NA>(tmem + ((unsigned)(warp * 32) << 16), v);
+    } else {
+#pragma unroll
+      for (int c = 0; c < NA; ++c) v[c] = 0.f;
+    }
+    umma_store_tile<NA>(o, nrow, N, v, stage + warp * 64 * N, n_stores, bulk_out);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  // leave only with nothing in flight that targets this CTA (bounded second waits)
+  if (failed && tid == 0) {
+    for (long long u = t; u < n_req; ++u)
+      mbar_wait(&full[u & 1], (unsigned)((u >> 1) & 1), nullptr, kWaitDrainNs);
+    if (t > 0) mbar_wait(&mma_done[(t - 1) & 1], (unsigned)(((t - 1) >> 1) & 1), nullptr,
+                         kWaitDrainNs);
+  }
+  if ((tid & 31) == 0) bulk_store_wait_all();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                  : "memory");
   }
 }
@@ -1555,65 +1906,124 @@ static bool level_tma_ok(const GemmDesc& g) {
   return g.hst->a4 && g.hst->b4;
 }
 
+// Tensor-memory columns of one CTA of the tensor-core grouped level stage: the group's items
+// (NA columns each) rounded up to a power of two, at most 128 (larger groups take passes), so
+// that up to four CTAs can share an SM's 512 columns.
+static int umma_level_cols(int sb_max, int na) {
+  const int need = (sb_max * na + 15) & ~15;
+  int c = 32;
+  while (c < need && c < 128) c *= 2;
+  return c;
+}
+
 // The tensor-core grouped level stage takes A-group launches the bulk-copy kernel takes, with
 // N <= 32 and K <= 64 (any K: the padding to a multiple of 8 is zero).
 static bool umma_level_ok(const GemmDesc& g) {
   if (g.st.n_grp <= 0 || g.K > 64 || level_tma_na(g.N) == 0 || !level_tma_ok(g)) return false;
-  const int kp = (g.K + 7) & ~7;
-  return umma_level_smem(g.K, kp, g.hst->grp_max * level_tma_na(g.N) + 8) <= 220 * 1024;
+  const int na = level_tma_na(g.N), kp = (g.K + 7) & ~7;
+  return umma_level_plan(g.K, kp, g.N, g.hst->grp_max, g.hst->grp_max * na + 8).total <=
+         200 * 1024;
 }
 
-// Dynamic shared memory for a launch of `kern` with `need` bytes, padded until at most
-// 512 / kUmmaCols CTAs fit on an SM, so that every CTA's tcgen05.alloc finds free columns.
-static size_t umma_launch_smem(const void* kern, size_t need, int device) {
+// Dynamic shared memory for a launch of `kern` with `need` bytes, and the CTAs per SM it allows.
+// Shared memory bounds the CTAs an SM can hold at floor(smem per SM / (bytes + reserved per
+// CTA)); the request is padded until that bound times `ncols` is at most the 512 tensor-memory
+// columns of an SM, so that every resident CTA's tcgen05.alloc finds free columns. The kernel
+// prefers the largest shared-memory carveout, and the persistent grid is SMs x that bound.
+static std::pair<size_t, int> umma_launch_smem(const void* kern, size_t need, int ncols,
+                                               int device) {
   static std::mutex mu;
-  static std::map<std::tuple<const void*, size_t, int>, size_t> memo;
+  static std::map<std::tuple<const void*, size_t, int, int>, std::pair<size_t, int>> memo;
   std::lock_guard<std::mutex> lock(mu);
-  const auto key = std::make_tuple(kern, need, device);
+  const auto key = std::make_tuple(kern, need, ncols, device);
   auto it = memo.find(key);
   if (it != memo.end()) return it->second;
-  int optin = 0;
+  int optin = 0, per_sm = 0, reserved = 0;
   CUDA_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+  CUDA_CHECK(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device));
+  CUDA_CHECK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device));
   cudaFuncAttributes fa{};
   CUDA_CHECK(cudaFuncGetAttributes(&fa, kern));
   const size_t dyn_max = (size_t)optin - fa.sharedSizeBytes;
   TTN_REQUIRE(need <= dyn_max, "tensor-core level kernel: %zu bytes of shared memory needed",
               need);
   CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max));
+  CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared));
+  auto fit = [&](size_t sm) {
+    return (int)((size_t)per_sm / (sm + fa.sharedSizeBytes + (size_t)reserved));
+  };
   size_t sm = need;
-  for (;;) {
-    int resident = 0;
-    CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kern, kUmmaRows, sm));
-    TTN_REQUIRE(resident >= 1, "tensor-core level kernel: does not fit on an SM");
-    if (resident * kUmmaCols <= 512) break;
-    sm += 4096;
+  while (fit(sm) * ncols > 512) {
+    sm += 1024;
     TTN_REQUIRE(sm <= dyn_max, "tensor-core level kernel: cannot bound CTAs per SM");
   }
-  memo[key] = sm;
-  return sm;
+  const int resident = fit(sm);
+  TTN_REQUIRE(resident >= 1, "tensor-core level kernel: does not fit on an SM");
+  memo[key] = {sm, resident};
+  return memo[key];
+}
+
+// The tensor-core segmented level stage takes the launches of the segmented bulk-copy path
+// (items summing several segments), with N <= 32 and K <= 64.
+static bool umma_seg_ok(const GemmDesc& g) {
+  if (g.st.n_grp > 0 || g.K > 64 || level_tma_na(g.N) == 0 || !level_tma_ok(g)) return false;
+  const int kp = (g.K + 7) & ~7;
+  return umma_seg_plan(g.K, kp, g.N, (level_tma_na(g.N) + 15) & ~15).total <= 200 * 1024;
+}
+
+static void launch_level_umma_seg(ttn_ctx* ctx, const GemmDesc& g) {
+  const int na = level_tma_na(g.N);
+  const int kp = (g.K + 7) & ~7;
+  const size_t need = umma_seg_plan(g.K, kp, g.N, (na + 15) & ~15).total;
+  const int rt = (g.M + kUmmaRows - 1) / kUmmaRows;
+  const long long n_work = (long long)rt * g.st.n_sub * g.n_pairs;
+  const bool bulk_out = g.N % 4 == 0 && g.c_pstride % 4 == 0 &&
+                        reinterpret_cast<uintptr_t>(g.C) % 16 == 0 && g.hst->c4;
+  const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
+  const double flops = 2.0 * g.M * g.N * (double)g.K * g.hst->n_seg * g.n_pairs;
+  static const char* nm[] = {"level_tc05_seg_8", "level_tc05_seg_16", "level_tc05_seg_24",
+                             "level_tc05_seg_32"};
+  LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(float)));
+  GemmDesc gd = g;
+  gd.wait_flag = ctx->d_wait;
+  auto go = [&](auto kern) {
+    const auto [sm, resident] = umma_launch_smem((const void*)kern, need, 32, ctx->device);
+    const long long grid = std::min<long long>(n_work, (long long)ctx->sm_count * resident);
+    kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, et ? 1 : 0,
+                                                         bulk_out ? 1 : 0, n_work);
+  };
+  switch (na) {
+    case 8: go(level_umma_seg_kernel<8>); break;
+    case 16: go(level_umma_seg_kernel<16>); break;
+    case 24: go(level_umma_seg_kernel<24>); break;
+    default: go(level_umma_seg_kernel<32>); break;
+  }
+  CUDA_LAUNCH_CHECK();
 }
 
 static void launch_level_umma(ttn_ctx* ctx, const GemmDesc& g) {
   const int na = level_tma_na(g.N);
   const int kp = (g.K + 7) & ~7;
-  const int nb_rows = g.hst->grp_max * na + 8;
-  const size_t need = umma_level_smem(g.K, kp, nb_rows);
+  const int sb_max = g.hst->grp_max;
+  const int nb_rows = sb_max * na + 8;
+  const int ncols = umma_level_cols(sb_max, na);
+  const size_t need = umma_level_plan(g.K, kp, g.N, sb_max, nb_rows).total;
   const int rt = (g.M + kUmmaRows - 1) / kUmmaRows;
-  const long long grid = (long long)rt * g.st.n_grp * g.n_pairs;
-  TTN_REQUIRE(grid <= 0x7fffffffLL, "level grid too large");
-  const bool vec4 = g.N == na && g.N % 4 == 0 && g.c_pstride % 4 == 0 &&
-                    reinterpret_cast<uintptr_t>(g.C) % 16 == 0 && g.hst->c4;
+  const long long n_work = (long long)rt * g.st.n_grp * g.n_pairs;
+  const bool bulk_out = g.N % 4 == 0 && g.c_pstride % 4 == 0 &&
+                        reinterpret_cast<uintptr_t>(g.C) % 16 == 0 && g.hst->c4;
   const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
   const double flops = 2.0 * g.M * g.N * (double)g.K * g.st.n_sub * g.n_pairs;
-  static const char* nm[] = {"level_umma_tf32x3_8", "level_umma_tf32x3_16",
-                             "level_umma_tf32x3_24", "level_umma_tf32x3_32"};
+  static const char* nm[] = {"level_tc05_8", "level_tc05_16", "level_tc05_24", "level_tc05_32"};
   LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(float)));
   GemmDesc gd = g;
   gd.wait_flag = ctx->d_wait;
   auto go = [&](auto kern) {
-    const size_t sm = umma_launch_smem((const void*)kern, need, ctx->device);
-    kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, nb_rows, et ? 1 : 0,
-                                                         vec4 ? 1 : 0);
+    const auto [sm, resident] = umma_launch_smem((const void*)kern, need, ncols, ctx->device);
+    const long long grid = std::min<long long>(n_work, (long long)ctx->sm_count * resident);
+    kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, sb_max, nb_rows, ncols,
+                                                         et ? 1 : 0, bulk_out ? 1 : 0, n_work);
   };
   switch (na) {
     case 8: go(level_umma_kernel<8>); break;
@@ -1633,6 +2043,10 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   const bool tc = sizeof(T) == 4 && ctx->tf32x3 && g.K % 8 == 0;
   if (sizeof(T) == 4 && ctx->tf32x3 && !(tc && level_tma_ok(g)) && level_tc_ok(g)) {
     launch_level_tc(ctx, g);
+    return;
+  }
+  if (sizeof(T) == 4 && ctx->tc05 && umma_seg_ok(g)) {
+    launch_level_umma_seg(ctx, g);
     return;
   }
   if (sizeof(T) == 4 && level_tma_ok(g) && g.st.n_grp == 0) {
@@ -1706,7 +2120,7 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     CUDA_LAUNCH_CHECK();
     return;
   }
-  if (sizeof(T) == 4 && ctx->tf32x3 && umma_level_ok(g)) {
+  if (sizeof(T) == 4 && ctx->tc05 && umma_level_ok(g)) {
     launch_level_umma(ctx, g);
     return;
   }

@@ -1797,7 +1797,7 @@ ttn_status ttn_recompress(ttn_ctx* ctx, int n_in, const double* coeff, const ttn
     TTN_REQUIRE(n_in >= 0 && (n_in == 0 || (coeff && ops && in && in_state)), "inputs");
     TTN_REQUIRE(n_out == out->n_states, "n_out must equal the states of `out`");
     TTN_REQUIRE(n_sweeps >= 0, "n_sweeps < 0");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     std::vector<FitGroup> groups;
     for (int k = 0; k < n_in; ++k) {
       check_block_like(in[k], out);
@@ -1837,7 +1837,7 @@ ttn_status ttn_als_solve(ttn_ctx* ctx, const ttn_ttno* H, const double* shift,
     TTN_REQUIRE(rhs->n_states == y->n_states, "rhs and y differ in state count");
     TTN_REQUIRE(H->tree.same_shape(y->tree), "operator on another tree");
     TTN_REQUIRE(n_sweeps >= 0 && minres_max >= 0 && minres_tol >= 0.0, "bad solver settings");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     std::vector<double> s(shift, shift + y->n_states);
     bool hit = prec == TTN_FP64
                    ? als_impl<double>(ctx, const_cast<ttn_ttno*>(H), s, rhs, y, n_sweeps,
@@ -1882,7 +1882,7 @@ ttn_status ttn_lobpcg(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, int n_iter,
                 "bad solver settings");
     TTN_REQUIRE(x->n_states >= 1, "empty block");
     TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     bool hit = false;
     if (prec == TTN_FP64)
       lobpcg_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, shift_offset, als_sweeps,
@@ -1908,7 +1908,7 @@ ttn_status ttn_inverse_iteration(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x, 
                 "bad solver settings");
     TTN_REQUIRE(x->n_states >= 1, "empty block");
     TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     bool hit = false;
     if (prec == TTN_FP64)
       inverse_iteration_impl<double>(ctx, const_cast<ttn_ttno*>(H), x, n_iter, cluster_gap,
@@ -1933,7 +1933,7 @@ ttn_status ttn_block_rayleigh_ritz(ttn_ctx* ctx, const ttn_ttno* Hc, ttn_block* 
     ttn_ttno* H = const_cast<ttn_ttno*>(Hc);
     TTN_REQUIRE(H->tree.same_shape(x->tree), "operator on another tree");
     TTN_REQUIRE(x->n_states >= 1 && fit_sweeps >= 1 && eps >= 0.0, "bad arguments");
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3, "unknown precision");
+    TTN_REQUIRE(valid_precision(prec), "unknown precision");
     ttn_ttno* Id = identity_for(ctx, x->tree);
     ttn_block* yb = nullptr;
     {
@@ -1966,7 +1966,7 @@ ttn_status ttn_src_apply(ttn_ctx* ctx, const ttn_ttno* Hc, const ttn_block* x, i
     const TreeInfo& tr = x->tree;
     TTN_REQUIRE(H->tree.same_shape(tr), "TTNO and block live on different trees");
     TTN_REQUIRE(chi >= 1 && chi <= 64, "chi = %d outside [1, 64]", chi);
-    TTN_REQUIRE(prec == TTN_FP64 || prec == TTN_FP32 || prec == TTN_TF32X3,
+    TTN_REQUIRE(valid_precision(prec),
                 "unknown precision %d", (int)prec);
     std::vector<std::vector<double>> om(tr.n);
     long long o = 0;

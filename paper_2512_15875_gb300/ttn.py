@@ -16,11 +16,12 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libttn.so")
 
-TTN_FP64, TTN_FP32, TTN_TF32X3 = 0, 1, 2
+TTN_FP64, TTN_FP32, TTN_TF32X3, TTN_TF32X3_TC05 = 0, 1, 2, 3
 TTN_MAX_LEGS = 8
 STATUS = {0: "TTN_OK", 1: "TTN_EINVAL", 2: "TTN_ENOMEM", 3: "TTN_ECUDA", 4: "TTN_ENONFINITE",
           5: "TTN_ENOTCONV", 6: "TTN_ETIMEOUT", 7: "TTN_EUNSUPPORTED"}
-PRECISION = {"fp64": TTN_FP64, "fp32": TTN_FP32, "tf32x3": TTN_TF32X3}
+PRECISION = {"fp64": TTN_FP64, "fp32": TTN_FP32, "tf32x3": TTN_TF32X3,
+             "tf32x3_tc05": TTN_TF32X3_TC05}
 
 _lib = None
 _P = C.c_void_p

@@ -30,7 +30,7 @@ def ctx(T):
 
 
 @pytest.mark.parametrize("name", ["c2", "c3", "c4", "c5"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 def test_full_size_gram_sampled(T, ctx, name, prec):
     w = I.make_workload(name)
     th = T.ttn_tree_create(ctx, w.tree)
@@ -52,7 +52,7 @@ def test_full_size_gram_sampled(T, ctx, name, prec):
 # --- element-wise parity at the benchmark size ------------------------------------------------
 
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_gram_252.npz")
-TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-5}
+TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-5, "tf32x3_tc05": 2e-5}
 
 
 def _c2_gold_block(name):
@@ -69,7 +69,7 @@ def _c2_gold_block(name):
 
 @pytest.mark.parametrize("workspace_gb", [None, "1.5"])
 @pytest.mark.parametrize("block", ["prod", "rand"])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 def test_c2_gram_every_entry_matches_the_oracle(T, ctx, prec, block, workspace_gb, monkeypatch):
     """All 31 878 pairs of the 252-state subspace of the 12-mode QFF (fork-4, D = 24) against the
     oracle's values stored by tests/golden/make_c2_gram.py, for near-product and dense random
@@ -102,7 +102,7 @@ def _import_ttno(T, ctx, th, tree, otn):
 
 
 @pytest.mark.parametrize("name,nodes", [("c2", (1, 5)), ("c5", (1,))])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 def test_full_size_environments_and_heff(T, ctx, name, nodes, prec):
     """Environments on every leg of a backbone node (two children, no physical leg) and of a
     chain node (one child and a physical leg) of the 12-mode QFF on the fork-4 tree at D = 24,

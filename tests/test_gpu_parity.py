@@ -8,8 +8,8 @@ which do not depend on any TTNO.
 Tolerances: FP64 path 1e-12 relative to the largest magnitude of the compared quantity (sums of
 at most a few 10^5 products of O(1) numbers in float64); FP32 path 2e-5 relative (float32
 accumulation of the same sums: ~1e-7 per operation grown by the contraction depth); the
-tensor-core path (3xTF32 split products, ~2^-21 per product, float32 accumulation) uses the
-float32 bound."""
+tensor-core paths (3xTF32 split products, ~2^-21 per product, float32 accumulation; mma.sync or
+tcgen05 kernels) use the float32 bound."""
 import numpy as np
 import pytest
 
@@ -18,7 +18,7 @@ from paper_2512_15875_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-5}
+TOL = {"fp64": 1e-12, "fp32": 2e-5, "tf32x3": 2e-5, "tf32x3_tc05": 2e-5}
 
 
 @pytest.fixture(scope="module")
@@ -90,7 +90,7 @@ def _rel(x, ref):
     return np.abs(x - ref).max() / max(np.abs(ref).max(), 1e-300)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_environments_match_oracle(T, ctx, case, prec):
     tree, ham, bonds, th, otn, H, A, B, bA, bB = _setup(T, ctx, case, 2, 3, seed=7)
@@ -111,7 +111,7 @@ def test_environments_match_oracle(T, ctx, case, prec):
             assert _rel(got_dn, ref_dn) <= TOL[prec], (t, "down")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_gram_matches_oracle(T, ctx, case, prec):
     tree, ham, bonds, th, otn, H, A, B, bA, bB = _setup(T, ctx, case, 3, 4, seed=11)
@@ -125,7 +125,7 @@ def test_gram_matches_oracle(T, ctx, case, prec):
             assert abs(S[i, j] - ref_s) <= TOL[prec] * np.abs(S).max() * 10, (i, j)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 def test_symmetric_gram_of_one_block(T, ctx, prec):
     case = CASES[1]
     tree, ham, bonds, th, otn, H, A, B, bA, bB = _setup(T, ctx, case, 5, 1, seed=13)
@@ -137,7 +137,7 @@ def test_symmetric_gram_of_one_block(T, ctx, prec):
     assert np.all(np.linalg.eigvalsh(S) > -1e-10 * np.abs(S).max())
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_heff_matches_oracle(T, ctx, case, prec):
     tree, ham, bonds, th, otn, H, A, B, bA, bB = _setup(T, ctx, case, 3, 3, seed=17)
@@ -155,7 +155,7 @@ def test_heff_matches_oracle(T, ctx, case, prec):
             assert _rel(got[s], ref) <= TOL[prec] * 10, (t, s)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 @pytest.mark.parametrize("case", CASES[:3], ids=[c[0] for c in CASES[:3]])
 def test_exact_apply_matches_oracle(T, ctx, case, prec):
     name, mk, d, D = case
@@ -226,7 +226,7 @@ def test_bad_arguments_are_reported(T, ctx):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "tf32x3_tc05"])
 def test_full_size_qff_gram_sampled(T, ctx, prec):
     """The 12-mode QFF on the fork-4 tree at D=24 with the 252-state subspace the LOBPCG Gram
     contracts (3 x 84 states): sampled entries against the term-by-term oracle."""
