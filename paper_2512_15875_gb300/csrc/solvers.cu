@@ -707,7 +707,10 @@ static int jacobi_grid_blocks(int device) {
   CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel, 256,
                                                            jacobi_smem(kJacobiMaxM)));
   CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-  int b = std::max(1, std::min(per_sm, 2) * sms);
+  // one CTA per SM: measured on the 300 x 300 Rayleigh-Ritz of block LOBPCG, two per SM made
+  // each grid barrier dearer (55 ms against 42 ms per call) and half as many made each round's
+  // share of the rotations dearer (55 ms)
+  int b = std::max(1, std::min(per_sm, 1) * sms);
   b = std::min(b, 1024);
   if (device >= 0 && device < 64) cached[device] = b;
   return b;
