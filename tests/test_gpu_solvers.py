@@ -166,7 +166,7 @@ def test_lobpcg_matches_oracle_fp64(T, ctx):
         assert _rel(hist[it], ref_hist[it]) <= 1e-10, it
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32x3_tc05"])
 def test_lobpcg_reduced_precision_within_a_tenth_of_a_wavenumber(T, ctx, prec):
     w, th, H = _c1(T, ctx)
     otn = N.build_ttno(w.tree, w.ham)
