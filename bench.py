@@ -74,6 +74,12 @@ def parse(argv=None):
     ap.add_argument("--ii-lobpcg", type=int, default=8,
                     help="inverse mode: LOBPCG iterations that make the starting states")
     ap.add_argument("--ref-max-iter", type=int, default=8)
+    ap.add_argument("--als-sweeps", type=int, default=2,
+                    help="ALS sweeps of the preconditioner solve per LOBPCG iteration")
+    ap.add_argument("--fit-sweeps", type=int, default=2,
+                    help="variational-fitting sweeps per fitted state")
+    ap.add_argument("--minres-max", type=int, default=10,
+                    help="MINRES iterations per local solve of the preconditioner")
     ap.add_argument("--profile-iters", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -328,7 +334,8 @@ def gpu_arm(args, rank, world, local, dist):
     th = T.ttn_tree_create(ctx, w.tree)
     H, wbond = T.ttn_build_ttno(ctx, th, w.ham.flat(w.tree))
     x0 = T.block_from_arrays(ctx, th, w.bonds, blk)
-    kw = dict(als_sweeps=2, minres_max=10, minres_tol=1e-5, fit_sweeps=2)
+    kw = dict(als_sweeps=args.als_sweeps, minres_max=args.minres_max, minres_tol=1e-5,
+              fit_sweeps=args.fit_sweeps)
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     mp = machine_peaks(n_sms, load_peaks())
 
@@ -725,6 +732,8 @@ def main():
                   "fp64": "f64"}[args.precision], "data": "synthetic",
         "config": {"workload": f"{args.workload}: {w.description}, the lowest {nw} states",
                    "block": nb, "guard_vectors": nb - nw, "subspace": 3 * nb,
+                   "als_sweeps": args.als_sweeps, "fit_sweeps": args.fit_sweeps,
+                   "minres_max": args.minres_max,
                    "ttno_max_bond": max(out["wbond"]),
                    "steps_are": "block-LOBPCG iterations from the initial block",
                    "l2": "working set (environments, intermediates) of several GB > 129 MB L2",

@@ -5,7 +5,10 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <set>
+
+#include <cuda.h>
 
 #include "internal.h"
 
@@ -243,6 +246,44 @@ static void smem_attr(const void* fn, int bytes, int device) {
   if (done.count({fn, device})) return;
   CUDA_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
   done.insert({fn, device});
+}
+
+// 2-D tensor maps for the tensor copies (cp.async.bulk.tensor) of row blocks: a buffer of float
+// rows, `row_len` elements per row, viewed as (row_len, rows); one box is box_x elements of
+// box_y consecutive rows, landing densely in shared memory. The encoder is the driver's
+// cuTensorMapEncodeTiled, reached through the runtime's entry-point query (no driver library
+// link). Returns false where the buffer cannot be described (alignment, sizes).
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                       const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                       const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+static TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<TensorMapEncodeFn>(p);
+  }();
+  return fn;
+}
+static bool make_row_tensor_map(CUtensorMap* m, const void* base, long long row_len, long long rows,
+                                int box_x, int box_y) {
+  const TensorMapEncodeFn enc = tensor_map_encoder();
+  if (!enc || reinterpret_cast<uintptr_t>(base) % 16 || row_len <= 0 || rows <= 0 ||
+      (row_len * 4) % 16 || box_x <= 0 || box_x > 256 || (box_x * 4) % 16 || box_y <= 0 ||
+      box_y > 256 || row_len >= (1LL << 31) || rows >= (1LL << 31))
+    return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)row_len, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)row_len * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Algorithmic bytes of a strided batched launch: the operands that are node tensors,
@@ -770,6 +811,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
+// global -> shared tensor copy of one box at element coordinates (x, y) of a 2-D tensor map
+// (x * 4 bytes a multiple of 16; the destination 128-byte aligned); elements outside the tensor
+// land as zeros and count towards the barrier's bytes like the others
+__device__ __forceinline__ void tensor_copy_g2s(void* dst, const CUtensorMap* map, int x, int y,
+                                                unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], "
+      "[%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
 // Orders earlier generic-proxy accesses of shared memory before later bulk copies into it.
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -987,10 +1039,11 @@ __device__ __forceinline__ void level_store(float* dst, int nrow, int N, const f
 // pair that read the same A slice: the A tile and every item's slice land on one mbarrier, each
 // slice is brought to the compute layout, and the items are computed one after the other from
 // the one staged tile.
-template <int NA, bool TC>
+template <int NA, bool TC, bool TMAP>
 __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, int rows_cta,
-                                                        int sb_max, int vec_store, int et) {
-  extern __shared__ __align__(16) float dsm[];
+                                                        int sb_max, int vec_store, int et,
+                                                        const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ __align__(128) float dsm[];
   __shared__ __align__(8) unsigned long long bar;
   const int lda = TC ? rows_cta + 8 : rows_cta;
   const int nk4 = (g.N * g.K + 3) & ~3;
@@ -1015,9 +1068,16 @@ __global__ void __launch_bounds__(288) level_tma_kernel(GemmDesc g, int rtiles, 
   __syncthreads();
   if (threadIdx.x == 0) {
     const float* Ab = Abase + g.st.grp_a[q] + r0;
-    mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
-    for (int b = 0; b < g.K; ++b)
-      bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
+    if (TMAP && (smem_addr(dsm) & 127u) == 0u) {
+      // the A tile as one tensor copy (a box of lda x K of the buffer's row view)
+      const long long oa = Abase + g.st.grp_a[q] - static_cast<const float*>(g.A.base);
+      mbar_expect_tx(&bar, (unsigned)(g.K * lda + ns * g.N * g.K) * 4u);
+      tensor_copy_g2s(As, &tmA, r0, (int)(oa / g.a_sk), &bar);
+    } else {
+      mbar_expect_tx(&bar, (unsigned)(g.K * nrow + ns * g.N * g.K) * 4u);
+      for (int b = 0; b < g.K; ++b)
+        bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &bar);
+    }
     for (int j = 0; j < ns; ++j)
       bulk_copy_g2s(Er + j * nk4, Bbase + g.st.grp_b[gs + j], g.N * g.K * 4u, &bar);
   }
@@ -1183,6 +1243,12 @@ __device__ __forceinline__ void level_mac_raw_tc(const float* As, int lda, const
   }
 }
 
+// Floats of one stage of the warp-specialised segmented level kernel: the A tile (K rows of lda)
+// and the slice (K x NA), rounded up to 128 bytes so that every stage starts 128-byte aligned.
+__host__ __device__ inline int seg_ws_stage_floats(int K, int lda, int na) {
+  return (K * lda + K * na + 31) & ~31;
+}
+
 // Segmented level stage, warp-specialised (slices stored [b][a] with N = NA, i.e. already in
 // the SIMT compute layout). Warps 0..nw-1 compute (32 rows each; float32 SIMT, or the
 // tensor-core 3xTF32 path when TC), warp nw produces: its first lane requests segment j's A
@@ -1190,11 +1256,15 @@ __device__ __forceinline__ void level_mac_raw_tc(const float* As, int lda, const
 // mbarrier with one arrival per compute warp), and the copies complete a "full" mbarrier the
 // compute warps wait on. No CTA-wide barrier inside the segment loop; every wait is bounded.
 // A tile rows are lda = rows_cta (+ 8 for TC) floats apart.
-template <int NA, bool TC>
+// TMAP: the A tile comes as one tensor copy (a box of lda x K from the row view of the A
+// buffer, rows a_sk floats long) instead of K row copies, where the destination is 128-byte
+// aligned (the row copies stand in otherwise).
+template <int NA, bool TC, bool TMAP>
 __device__ __forceinline__ bool seg_ws_pipeline(const GemmDesc& g, float* dsm, int rows_cta,
                                                 int lda, int stage, int pair, int s0, int nseg,
                                                 int r0, int nrow, unsigned long long* full,
-                                                unsigned long long* empty, float* acc) {
+                                                unsigned long long* empty, float* acc,
+                                                const CUtensorMap* tmA) {
   const int nw = rows_cta >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == nw) {
@@ -1208,9 +1278,15 @@ __device__ __forceinline__ bool seg_ws_pipeline(const GemmDesc& g, float* dsm, i
         float* As = dsm + st * stage;
         float* Es = As + g.K * lda;
         const float* Ab = Abase + g.st.seg_a[s0 + j] + r0;
-        mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
-        for (int b = 0; b < g.K; ++b)
-          bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
+        if (TMAP && (smem_addr(dsm) & 127u) == 0u) {
+          const long long oa = Abase + g.st.seg_a[s0 + j] - static_cast<const float*>(g.A.base);
+          mbar_expect_tx(&full[st], (unsigned)(g.K * lda + g.N * g.K) * 4u);
+          tensor_copy_g2s(As, tmA, r0, (int)(oa / g.a_sk), &full[st]);
+        } else {
+          mbar_expect_tx(&full[st], (unsigned)(g.K * nrow + g.N * g.K) * 4u);
+          for (int b = 0; b < g.K; ++b)
+            bulk_copy_g2s(As + b * lda, Ab + (long long)b * g.a_sk, nrow * 4u, &full[st]);
+        }
         bulk_copy_g2s(Es, Bbase + g.st.seg_b[s0 + j], g.N * g.K * 4u, &full[st]);
       }
     }
@@ -1233,15 +1309,16 @@ __device__ __forceinline__ bool seg_ws_pipeline(const GemmDesc& g, float* dsm, i
   return true;
 }
 
-template <int NA, bool TC>
+template <int NA, bool TC, bool TMAP>
 __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtiles, int rows_cta,
-                                                           int vec_store) {
-  extern __shared__ __align__(16) float dsm[];
+                                                           int vec_store,
+                                                           const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ __align__(128) float dsm[];
   __shared__ __align__(8) unsigned long long full[2];
   __shared__ __align__(8) unsigned long long empty[2];
   const int nw = rows_cta >> 5;
   const int lda = rows_cta + (TC ? 8 : 0);
-  const int stage = g.K * lda + g.K * NA;
+  const int stage = seg_ws_stage_floats(g.K, lda, NA);
   const long long bid = blockIdx.x;
   const int rt = (int)(bid % rtiles);
   const long long rest = bid / rtiles;
@@ -1259,8 +1336,8 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
   }
   __syncthreads();
   float acc[NA];
-  if (!seg_ws_pipeline<NA, TC>(g, dsm, rows_cta, lda, stage, pair, s0, nseg, r0, nrow, full,
-                               empty, acc))
+  if (!seg_ws_pipeline<NA, TC, TMAP>(g, dsm, rows_cta, lda, stage, pair, s0, nseg, r0, nrow,
+                                     full, empty, acc, &tmA))
     return;
   if ((threadIdx.x >> 5) * 32 >= nrow) return;
   long long cidx = 0;
@@ -1865,7 +1942,19 @@ int level_tma_rows(int M) {
   const int ncta = (nwt + 8) / 9;
   return (nwt + ncta - 1) / ncta * 32;
 }
+// row tile of at most maxw warps, the tiles of M as even as whole warps allow
+int level_tma_rows_cap(int M, int maxw) {
+  const int nwt = (M + 31) / 32;
+  const int ncta = (nwt + maxw - 1) / maxw;
+  return (nwt + ncta - 1) / ncta * 32;
+}
 int level_env_floats_host(int NA, bool tc, int K) { return tc ? 2 * NA * (K + 4) : K * NA; }
+size_t level_tma_smem_rows(int rows, int N, int K, int sb, bool tc) {
+  const int na = level_tma_na(N);
+  const int lda = rows + (tc ? 8 : 0);
+  return sizeof(float) * ((size_t)K * lda + (size_t)sb * ((N * K + 3) & ~3) +
+                          (size_t)sb * level_env_floats_host(na, tc, K));
+}
 size_t level_tma_smem(int M, int N, int K, int sb, bool tc) {
   const int na = level_tma_na(N);
   const int lda = level_tma_rows(M) + (tc ? 8 : 0);
@@ -1904,6 +1993,19 @@ static bool level_tma_ok(const GemmDesc& g) {
   if (reinterpret_cast<uintptr_t>(g.A.base) % 16 || reinterpret_cast<uintptr_t>(g.B.base) % 16)
     return false;
   return g.hst->a4 && g.hst->b4;
+}
+
+// Tensor map of a level stage's A operand (K slices of a_sk contiguous floats per item) as a
+// row view of its buffer, boxes of box_x x K: only where every item's block starts a row of the
+// buffer and the buffer holds whole rows.
+static bool level_a_tensor_map(const GemmDesc& g, int box_x, CUtensorMap* tm) {
+  if (box_x > 256 || g.K > 256 || g.a_sm != 1 || g.a_sk <= 0 || g.a_len % g.a_sk) return false;
+  if (g.A.mode != MODE_CONST && g.A.pstride % g.a_sk) return false;
+  for (long long a : g.hst->seg_a)
+    if (a % g.a_sk) return false;
+  for (long long a : g.hst->grp_a)
+    if (a % g.a_sk) return false;
+  return make_row_tensor_map(tm, g.A.base, g.a_sk, g.a_len / g.a_sk, box_x, g.K);
 }
 
 // Tensor-memory columns of one CTA of the tensor-core grouped level stage: the group's items
@@ -2071,29 +2173,36 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
     const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
     if (et && g.N == na) {
       // slices already in the SIMT compute layout: warp-specialised copy/compute pipeline
-      // (float32 SIMT, or 3xTF32 tensor cores with A rows padded by 8 floats)
-      const size_t lda = (size_t)rows_cta + (tc ? 8 : 0);
-      const size_t smem_ws = sizeof(float) * 2 * ((size_t)g.K * lda + (size_t)g.K * na);
+      // (float32 SIMT, or 3xTF32 tensor cores with A rows padded by 8 floats). Where the A
+      // buffer has a tensor-map row view, tiles of at most 8 warps (the box holds at most 256
+      // columns) come as one tensor copy each.
+      CUtensorMap tmA{};
+      int rows_ws = level_tma_rows_cap(g.M, 8);
+      const bool tmap = level_a_tensor_map(g, rows_ws + (tc ? 8 : 0), &tmA);
+      if (!tmap) rows_ws = rows_cta;
+      const int rt_ws = (g.M + rows_ws - 1) / rows_ws;
+      const long long grid_ws = (long long)rt_ws * g.st.n_sub * g.n_pairs;
+      TTN_REQUIRE(grid_ws <= 0x7fffffffLL, "level grid too large");
+      const int lda = rows_ws + (tc ? 8 : 0);
+      const size_t smem_ws = sizeof(float) * 2 * (size_t)seg_ws_stage_floats(g.K, lda, na);
       auto go_ws = [&](auto kern) {
         smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
-        kern<<<(unsigned)grid, rows_cta + 32, smem_ws, ctx->stream>>>(gd, rt, rows_cta,
-                                                                        vec ? 1 : 0);
+        kern<<<(unsigned)grid_ws, rows_ws + 32, smem_ws, ctx->stream>>>(gd, rt_ws, rows_ws,
+                                                                          vec ? 1 : 0, tmA);
       };
-      if (tc) {
+      auto pick = [&](auto t_tc, auto t_map) {
+        constexpr bool TCv = decltype(t_tc)::value, TMv = decltype(t_map)::value;
         switch (na) {
-          case 8: go_ws(level_seg_ws_kernel<8, true>); break;
-          case 16: go_ws(level_seg_ws_kernel<16, true>); break;
-          case 24: go_ws(level_seg_ws_kernel<24, true>); break;
-          default: go_ws(level_seg_ws_kernel<32, true>); break;
+          case 8: go_ws(level_seg_ws_kernel<8, TCv, TMv>); break;
+          case 16: go_ws(level_seg_ws_kernel<16, TCv, TMv>); break;
+          case 24: go_ws(level_seg_ws_kernel<24, TCv, TMv>); break;
+          default: go_ws(level_seg_ws_kernel<32, TCv, TMv>); break;
         }
-      } else {
-        switch (na) {
-          case 8: go_ws(level_seg_ws_kernel<8, false>); break;
-          case 16: go_ws(level_seg_ws_kernel<16, false>); break;
-          case 24: go_ws(level_seg_ws_kernel<24, false>); break;
-          default: go_ws(level_seg_ws_kernel<32, false>); break;
-        }
-      }
+      };
+      using T_ = std::true_type;
+      using F_ = std::false_type;
+      if (tc) tmap ? pick(T_{}, T_{}) : pick(T_{}, F_{});
+      else tmap ? pick(F_{}, T_{}) : pick(F_{}, F_{});
       CUDA_LAUNCH_CHECK();
       return;
     }
@@ -2126,10 +2235,15 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
   }
   if (sizeof(T) == 4 && level_tma_ok(g)) {
     const int na = level_tma_na(g.N);
-    const int rows_cta = level_tma_rows(g.M);
+    // tiles of at most 8 warps with the A tile as one tensor copy where the A buffer has a
+    // tensor-map row view (a box holds at most 256 columns), else up to 9 warps and row copies
+    CUtensorMap tmA{};
+    int rows_cta = level_tma_rows_cap(g.M, 8);
+    const bool tmap = level_a_tensor_map(g, rows_cta + (tc ? 8 : 0), &tmA);
+    if (!tmap) rows_cta = level_tma_rows(g.M);
     const int rt = (g.M + rows_cta - 1) / rows_cta;
     const int sb_max = g.hst->grp_max;
-    const size_t smem = level_tma_smem(g.M, g.N, g.K, sb_max, tc);
+    const size_t smem = level_tma_smem_rows(rows_cta, g.N, g.K, sb_max, tc);
     TTN_REQUIRE(smem <= kLevelTmaSmem, "level kernel: A group larger than its cap");
     bool vec = g.N == na && g.c_pstride % 2 == 0 &&
                reinterpret_cast<uintptr_t>(g.C) % 8 == 0;
@@ -2149,23 +2263,21 @@ void launch_level(ttn_ctx* ctx, const GemmDesc& g) {
       smem_attr((const void*)kern, (int)kLevelTmaSmem, ctx->device);
       const bool et = g.b_sn == 1 && g.b_sk == g.N && g.K != 1;
       kern<<<(unsigned)grid, threads, smem, ctx->stream>>>(gd, rt, rows_cta, sb_max, vec ? 1 : 0,
-                                                           et ? 1 : 0);
+                                                           et ? 1 : 0, tmA);
     };
-    if (tc) {
+    auto pick = [&](auto t_tc, auto t_map) {
+      constexpr bool TCv = decltype(t_tc)::value, TMv = decltype(t_map)::value;
       switch (na) {
-        case 8: go(level_tma_kernel<8, true>); break;
-        case 16: go(level_tma_kernel<16, true>); break;
-        case 24: go(level_tma_kernel<24, true>); break;
-        default: go(level_tma_kernel<32, true>); break;
+        case 8: go(level_tma_kernel<8, TCv, TMv>); break;
+        case 16: go(level_tma_kernel<16, TCv, TMv>); break;
+        case 24: go(level_tma_kernel<24, TCv, TMv>); break;
+        default: go(level_tma_kernel<32, TCv, TMv>); break;
       }
-    } else {
-      switch (na) {
-        case 8: go(level_tma_kernel<8, false>); break;
-        case 16: go(level_tma_kernel<16, false>); break;
-        case 24: go(level_tma_kernel<24, false>); break;
-        default: go(level_tma_kernel<32, false>); break;
-      }
-    }
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    if (tc) tmap ? pick(T_{}, T_{}) : pick(T_{}, F_{});
+    else tmap ? pick(F_{}, T_{}) : pick(F_{}, F_{});
     CUDA_LAUNCH_CHECK();
     return;
   }
@@ -2278,6 +2390,13 @@ __global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
 }
 
 
+// Shared-memory layout of one closure stage (floats): A rows at pitch ldk, then Z rows from the
+// next 128-byte boundary, the stage rounded up to 128 bytes (tensor copies land 128-byte aligned).
+__host__ __device__ inline int closure_z_offset(int mp, int ldk) { return (mp * ldk + 31) & ~31; }
+__host__ __device__ inline int closure_stage_floats(int mp, int np, int ldk) {
+  return (closure_z_offset(mp, ldk) + np * ldk + 31) & ~31;
+}
+
 // Closure GEMM with bulk-copied operands (float32): C[a][b] = sum_k A[a][k] Z[b][k] for one
 // item per CTA, M, N <= MP, NP. K is cut into chunks of kc_max (a multiple of 8) that land in
 // shared memory (rows padded to kc_max + 4 floats, so 16-byte loads of 8 consecutive rows hit
@@ -2285,22 +2404,42 @@ __global__ void __launch_bounds__(kThreads) closure_kernel(GemmDesc g) {
 // flight while chunk c + 1 waits and chunk c is consumed. Each thread owns a TA x TB output tile
 // and one of NS interleaved k-slices; the slice partials are summed in a fixed order through
 // shared memory (aliasing the ring) at the end.
-template <int TA, int TB, int MP, int NP>
-__global__ void __launch_bounds__(kThreads, 3) closure_tma_kernel(GemmDesc g, int kc_max, int nstage) {
+template <int TA, int TB, int MP, int NP, bool TMAP>
+__global__ void __launch_bounds__(kThreads, 3)
+    closure_tma_kernel(GemmDesc g, int kc_max, int nstage, const __grid_constant__ CUtensorMap tmA,
+                       const __grid_constant__ CUtensorMap tmZ) {
   constexpr int NT = (MP / TA) * (NP / TB), NS = kThreads / NT;
-  extern __shared__ __align__(16) float dsm[];
+  extern __shared__ __align__(128) float dsm[];
   __shared__ __align__(8) unsigned long long bar[2];
-  const int ldk = kc_max + 4, stage = (MP + NP) * ldk;
+  const int ldk = kc_max + 4;
+  const int zoff = closure_z_offset(MP, ldk), stage = closure_stage_floats(MP, NP, ldk);
   const int sub = (int)(blockIdx.x % g.st.n_sub);
   const int pair = (int)(blockIdx.x / g.st.n_sub);
   const int seg = g.st.seg_ptr[sub];
   const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[seg];
   const float* Zb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[seg];
   const int nchunk = (g.K + kc_max - 1) / kc_max;
+  // first row of the item's A and Z blocks in the tensor maps' row view
+  int ya = 0, yz = 0;
+  if (TMAP && threadIdx.x == 0) {
+    ya = (int)((Ab - static_cast<const float*>(g.A.base)) / g.a_sm);
+    yz = (int)((Zb - static_cast<const float*>(g.B.base)) / g.b_sn);
+  }
   auto issue = [&](int c, int s) {
     const int k0 = c * kc_max, kc = min(kc_max, g.K - k0);
     float* As = dsm + s * stage;
-    float* Zs = As + MP * ldk;
+    float* Zs = As + zoff;
+    if constexpr (TMAP) {
+      // one box of (kc_max + 4) x M (x N) per operand: the rows land at pitch ldk, the 4 extra
+      // columns (next row or zeros past the end) are never read. Tensor copies need 128-byte
+      // aligned destinations: the row copies below stand in if the dynamic shared memory is not.
+      if ((smem_addr(dsm) & 127u) == 0u) {
+        mbar_expect_tx(&bar[s], (unsigned)((g.M + g.N) * ldk) * 4u);
+        tensor_copy_g2s(As, &tmA, k0, ya, &bar[s]);
+        tensor_copy_g2s(Zs, &tmZ, k0, yz, &bar[s]);
+        return;
+      }
+    }
     mbar_expect_tx(&bar[s], (unsigned)((g.M + g.N) * kc) * 4u);
     for (int r = 0; r < g.M; ++r)
       bulk_copy_g2s(As + r * ldk, Ab + (long long)r * g.a_sm + k0, kc * 4u, &bar[s]);
@@ -2332,7 +2471,7 @@ __global__ void __launch_bounds__(kThreads, 3) closure_tma_kernel(GemmDesc g, in
     if (__syncthreads_or(!ok)) return;
     const int kc = min(kc_max, g.K - c * kc_max);
     const float* As = dsm + s * stage;
-    const float* Zs = As + MP * ldk;
+    const float* Zs = As + zoff;
     if (ks < NS) {
       for (int qk = ks; qk < kc / 4; qk += NS) {
         const int k = qk * 4;
@@ -2397,11 +2536,29 @@ size_t closure_tma_smem(int K, int pad) {
   int kc_max, nstage;
   closure_tma_chunks(K, kc_max, nstage);
   const int nt = pad == 12 ? 16 : pad == 24 ? 16 : 32;
-  const size_t ring = (size_t)nstage * 2 * pad * (kc_max + 4);
+  const size_t ring = (size_t)nstage * closure_stage_floats(pad, pad, kc_max + 4);
   const size_t red = (size_t)(kThreads / nt) * pad * pad;
   return sizeof(float) * std::max(ring, red);
 }
 }  // namespace
+
+// Tensor maps of the closure operands (A rows of a_sm floats, Z rows of b_sn floats, boxes of
+// kc_max + 4 columns): only where every item's block starts a row of its buffer (so a box never
+// wraps into the next row's data at its start), the buffers hold whole rows and the box fits.
+static bool closure_tensor_maps(const GemmDesc& g, int kc_max, CUtensorMap* tmA, CUtensorMap* tmZ) {
+  const int box_x = kc_max + 4;
+  if (box_x > 256 || g.M > 256 || g.N > 256 || g.a_sm <= 0 || g.b_sn <= 0) return false;
+  if (g.a_len % g.a_sm || g.b_len % g.b_sn) return false;
+  if ((g.A.mode != MODE_CONST && g.A.pstride % g.a_sm) ||
+      (g.B.mode != MODE_CONST && g.B.pstride % g.b_sn))
+    return false;
+  for (long long a : g.hst->seg_a)
+    if (a % g.a_sm) return false;
+  for (long long b : g.hst->seg_b)
+    if (b % g.b_sn) return false;
+  return make_row_tensor_map(tmA, g.A.base, g.a_sm, g.a_len / g.a_sm, box_x, g.M) &&
+         make_row_tensor_map(tmZ, g.B.base, g.b_sn, g.b_len / g.b_sn, box_x, g.N);
+}
 
 // True if a float32 closure launch meets the bulk-copy kernel's layout and alignment needs.
 static bool closure_tma_ok(const GemmDesc& g) {
@@ -2532,16 +2689,24 @@ void launch_closure(ttn_ctx* ctx, const GemmDesc& g) {
     int kc_max, nstage;
     closure_tma_chunks(g.K, kc_max, nstage);
     const size_t smem = closure_tma_smem(g.K, pad);
+    CUtensorMap tmA{}, tmZ{};
+    const bool tma = closure_tensor_maps(g, kc_max, &tmA, &tmZ);
     LaunchScope ls(ctx, "closure_tma_f32", flops, bytes);
     GemmDesc gd = g;
     gd.wait_flag = ctx->d_wait;
     auto go = [&](auto kern) {
       smem_attr((const void*)kern, (int)kClosureTmaSmem, ctx->device);
-      kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(gd, kc_max, nstage);
+      kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(gd, kc_max, nstage, tmA, tmZ);
     };
-    if (pad == 12) go(closure_tma_kernel<3, 3, 12, 12>);
-    else if (pad == 24) go(closure_tma_kernel<6, 6, 24, 24>);
-    else go(closure_tma_kernel<4, 8, 32, 32>);
+    if (tma) {
+      if (pad == 12) go(closure_tma_kernel<3, 3, 12, 12, true>);
+      else if (pad == 24) go(closure_tma_kernel<6, 6, 24, 24, true>);
+      else go(closure_tma_kernel<4, 8, 32, 32, true>);
+    } else {
+      if (pad == 12) go(closure_tma_kernel<3, 3, 12, 12, false>);
+      else if (pad == 24) go(closure_tma_kernel<6, 6, 24, 24, false>);
+      else go(closure_tma_kernel<4, 8, 32, 32, false>);
+    }
     CUDA_LAUNCH_CHECK();
     return;
   }
