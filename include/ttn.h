@@ -309,9 +309,9 @@ ttn_status ttn_block_rayleigh_ritz(ttn_ctx* ctx, const ttn_ttno* H, ttn_block* x
  * library: about 3.7 MB of float64 per GPU, held from library load until process exit. The call
  * allocates and frees no device memory (no cudaMalloc, no pool allocation).
  *   - m may not exceed TTN_RR_NOALLOC_MAX_M; larger m returns TTN_EINVAL with a message.
- *   - The first call on each device looks up the area's device address (once per device, with
- *     that device made current for the lookup); make that first call before any stream
- *     capture on the device.
+ *   - ttn_create looks up the area's device address and loads the kernels this call launches
+ *     (under lazy module loading a kernel's first launch would load its code and take device
+ *     memory for it), once per device, so that no call, the first included, allocates.
  *   - All calls on a device share the one area and it keeps the last call's contents (every
  *     value a call reads there, it has written first). Calls that overlap on the GPU (other
  *     streams, other threads) race on it: serialise them.

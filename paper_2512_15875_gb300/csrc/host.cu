@@ -704,6 +704,7 @@ ttn_status ttn_create(ttn_ctx** out, int device, void* cuda_stream) {
     CUDA_CHECK(cudaHostGetDevicePointer(&dw, hw, 0));
     ctx->d_wait = static_cast<unsigned*>(dw);
     if (const char* lp = getenv("TTN_LAUNCH_LOG")) ctx->launch_log = std::fopen(lp, "a");
+    rr_noalloc_prepare(device);
     cudaMemPool_t pool;
     CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, device));
     uint64_t thr = UINT64_MAX;

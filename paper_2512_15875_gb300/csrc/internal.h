@@ -123,6 +123,8 @@ struct ttn_ctx {
 };
 
 // Records the iteration clock's start (mark 0 .. ) on the context stream.
+// Prepares ttn_rayleigh_ritz_noalloc on the current device (see solvers.cu).
+void rr_noalloc_prepare(int device);
 void iter_clock_start(ttn_ctx* ctx);
 void iter_clock_mark(ttn_ctx* ctx);
 

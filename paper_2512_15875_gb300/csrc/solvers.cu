@@ -1768,15 +1768,26 @@ double* g_rr_scratch_dev[kMaxDevices] = {nullptr};
 std::once_flag g_rr_once[kMaxDevices];
 cudaError_t g_rr_setup_err[kMaxDevices] = {cudaSuccess};
 
-// Device address of the working area on `device` (which must be current). Done once per
-// device; the host-side name of a __device__ array is only a stand-in, so the address has to
-// come from cudaGetSymbolAddress.
+// Device address of the working area on `device` (which must be current), and the kernels of
+// the no-allocation call loaded: under lazy module loading a kernel's code is loaded, and device
+// memory taken for it, at its first launch, which must not happen inside a no-allocation call.
+// Done once per device, when a context is created on it (and, failing that, at the first call);
+// the host-side name of a __device__ array is only a stand-in, so the address has to come from
+// cudaGetSymbolAddress.
 double* rr_scratch_for(int device) {
   TTN_REQUIRE(device >= 0 && device < kMaxDevices, "device %d out of range", device);
   std::call_once(g_rr_once[device], [device] {
     void* p = nullptr;
     g_rr_setup_err[device] = cudaGetSymbolAddress(&p, g_rr_scratch);
     if (g_rr_setup_err[device] == cudaSuccess) g_rr_scratch_dev[device] = static_cast<double*>(p);
+    const void* kernels[] = {(const void*)symmetrize_kernel, (const void*)jacobi_kernel,
+                             (const void*)sort_eig_kernel, (const void*)canon_basis_kernel,
+                             (const void*)small_gemm_kernel, (const void*)fix_sign_kernel};
+    for (const void* k : kernels) {
+      cudaFuncAttributes fa;
+      if (g_rr_setup_err[device] == cudaSuccess)
+        g_rr_setup_err[device] = cudaFuncGetAttributes(&fa, k);
+    }
   });
   if (g_rr_setup_err[device] != cudaSuccess)
     TTN_FAIL(TTN_ECUDA, "cudaGetSymbolAddress of the Rayleigh-Ritz working area failed: %s",
@@ -1785,6 +1796,10 @@ double* rr_scratch_for(int device) {
 }
 
 }  // namespace
+
+// Called when a context is created on `device` (current): prepares the no-allocation
+// Rayleigh-Ritz there (working-area address, its kernels loaded).
+void rr_noalloc_prepare(int device) { rr_scratch_for(device); }
 
 // ------------------------------------------------------------------------------------------------
 // C ABI
