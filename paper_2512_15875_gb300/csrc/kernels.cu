@@ -1551,7 +1551,9 @@ template <int NA>
 __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles, int kp,
                                                          int sb_max, int nb_rows, int ncols,
                                                          int et, int bulk_out,
-                                                         long long n_work) {
+                                                         long long n_work,
+                                                         const __grid_constant__ CUtensorMap tmA,
+                                                         int use_tmap) {
   extern __shared__ __align__(128) unsigned char usm[];
   __shared__ __align__(8) unsigned long long bar_ld;
   __shared__ __align__(8) unsigned long long bar_mma;
@@ -1601,9 +1603,16 @@ __global__ void __launch_bounds__(128) level_umma_kernel(GemmDesc g, int rtiles,
     const int gs = g.st.grp_ptr[q], ns = g.st.grp_ptr[q + 1] - gs;
     const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.grp_a[q] + r0;
     const float* Bb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket);
-    mbar_expect_tx(&bar_ld, (unsigned)(K * nrow + ns * N * K) * 4u);
-    for (int b = 0; b < K; ++b)
-      bulk_copy_g2s(As + b * kUmmaRows, Ab + (long long)b * g.a_sk, nrow * 4u, &bar_ld);
+    if (use_tmap && (smem_addr(As) & 127u) == 0u) {
+      // the A tile as one tensor copy (a box of 128 x K of the buffer's row view)
+      mbar_expect_tx(&bar_ld, (unsigned)(K * kUmmaRows + ns * N * K) * 4u);
+      tensor_copy_g2s(As, &tmA, r0,
+                      (int)((Ab - r0 - static_cast<const float*>(g.A.base)) / g.a_sk), &bar_ld);
+    } else {
+      mbar_expect_tx(&bar_ld, (unsigned)(K * nrow + ns * N * K) * 4u);
+      for (int b = 0; b < K; ++b)
+        bulk_copy_g2s(As + b * kUmmaRows, Ab + (long long)b * g.a_sk, nrow * 4u, &bar_ld);
+    }
     for (int j = 0; j < ns; ++j)
       bulk_copy_g2s(Er + j * nk4, Bb + g.st.grp_b[gs + j], N * K * 4u, &bar_ld);
   };
@@ -1748,7 +1757,9 @@ __host__ __device__ inline UmmaSegSmem umma_seg_plan(int K, int kp, int N, int n
 template <int NA>
 __global__ void __launch_bounds__(128) level_umma_seg_kernel(GemmDesc g, int rtiles, int kp,
                                                              int et, int bulk_out,
-                                                             long long n_work) {
+                                                             long long n_work,
+                                                             const __grid_constant__ CUtensorMap tmA,
+                                                             int use_tmap) {
   constexpr int NB = (NA + 15) & ~15;   // B rows = accumulator columns
   constexpr int kCols = 32;             // tensor-memory allocation (>= NB, a power of two)
   static_assert(NB <= kCols, "accumulator wider than its allocation");
@@ -1810,9 +1821,15 @@ __global__ void __launch_bounds__(128) level_umma_seg_kernel(GemmDesc g, int rti
     float* Es = As + K * kUmmaRows;
     const float* Ab = operand_base<float>(g.A, pair, g.pair_bra, g.pair_ket) + g.st.seg_a[sg] + r0;
     const float* Bb = operand_base<float>(g.B, pair, g.pair_bra, g.pair_ket) + g.st.seg_b[sg];
-    mbar_expect_tx(&full[b], (unsigned)(K * nrow + N * K) * 4u);
-    for (int kb = 0; kb < K; ++kb)
-      bulk_copy_g2s(As + kb * kUmmaRows, Ab + (long long)kb * g.a_sk, nrow * 4u, &full[b]);
+    if (use_tmap && (smem_addr(As) & 127u) == 0u) {
+      mbar_expect_tx(&full[b], (unsigned)(K * kUmmaRows + N * K) * 4u);
+      tensor_copy_g2s(As, &tmA, r0,
+                      (int)((Ab - r0 - static_cast<const float*>(g.A.base)) / g.a_sk), &full[b]);
+    } else {
+      mbar_expect_tx(&full[b], (unsigned)(K * nrow + N * K) * 4u);
+      for (int kb = 0; kb < K; ++kb)
+        bulk_copy_g2s(As + kb * kUmmaRows, Ab + (long long)kb * g.a_sk, nrow * 4u, &full[b]);
+    }
     bulk_copy_g2s(Es, Bb, N * K * 4u, &full[b]);
     if (++rq_s == nseg_of(rq_w)) {
       rq_s = 0;
@@ -2089,11 +2106,14 @@ static void launch_level_umma_seg(ttn_ctx* ctx, const GemmDesc& g) {
   LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(float)));
   GemmDesc gd = g;
   gd.wait_flag = ctx->d_wait;
+  CUtensorMap tmA{};
+  const bool tmap = level_a_tensor_map(g, kUmmaRows, &tmA);
   auto go = [&](auto kern) {
     const auto [sm, resident] = umma_launch_smem((const void*)kern, need, 32, ctx->device);
     const long long grid = std::min<long long>(n_work, (long long)ctx->sm_count * resident);
     kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, et ? 1 : 0,
-                                                         bulk_out ? 1 : 0, n_work);
+                                                         bulk_out ? 1 : 0, n_work, tmA,
+                                                         tmap ? 1 : 0);
   };
   switch (na) {
     case 8: go(level_umma_seg_kernel<8>); break;
@@ -2121,11 +2141,14 @@ static void launch_level_umma(ttn_ctx* ctx, const GemmDesc& g) {
   LaunchScope ls(ctx, nm[na / 8 - 1], flops, algorithmic_bytes(g, sizeof(float)));
   GemmDesc gd = g;
   gd.wait_flag = ctx->d_wait;
+  CUtensorMap tmA{};
+  const bool tmap = level_a_tensor_map(g, kUmmaRows, &tmA);
   auto go = [&](auto kern) {
     const auto [sm, resident] = umma_launch_smem((const void*)kern, need, ncols, ctx->device);
     const long long grid = std::min<long long>(n_work, (long long)ctx->sm_count * resident);
     kern<<<(unsigned)grid, kUmmaRows, sm, ctx->stream>>>(gd, rt, kp, sb_max, nb_rows, ncols,
-                                                         et ? 1 : 0, bulk_out ? 1 : 0, n_work);
+                                                         et ? 1 : 0, bulk_out ? 1 : 0, n_work,
+                                                         tmA, tmap ? 1 : 0);
   };
   switch (na) {
     case 8: go(level_umma_kernel<8>); break;
