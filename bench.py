@@ -232,13 +232,39 @@ def machine_peaks(n_sms, peaks):
     }
 
 
-def source_digest():
-    """Digest of the contraction kernels' sources (kernels.cu, internal.h); DRAM counters taken
-    on other sources are not reused."""
+def _code_only(text):
+    """C++ source without comments and blank space (string literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"':
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def source_digest(texts=None):
+    """Digest of the contraction kernels' code (kernels.cu, internal.h, comments and blank space
+    left out); DRAM counters taken on other code are not reused."""
+    if texts is None:
+        csrc = os.path.join(ROOT, "paper_2512_15875_gb300", "csrc")
+        texts = [open(os.path.join(csrc, f), encoding="utf-8").read()
+                 for f in ("kernels.cu", "internal.h")]
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2512_15875_gb300", "csrc")
-    for f in ("kernels.cu", "internal.h"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for t in texts:
+        h.update(_code_only(t).encode())
     return h.hexdigest()[:16]
 
 

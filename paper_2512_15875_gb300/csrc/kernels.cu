@@ -1352,8 +1352,9 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
 // ---- level stage on the fifth-generation tensor cores (tcgen05.mma, tensor-memory accumulators)
 // The grouped level stage C_j[r][a] = sum_b A[b][r] E_j[a][b] of one A group (the items j that
 // read the same A slice, i.e. the children of one prefix in the TTNO trie) for a 128-row tile:
-//  * the A tile (K slices of up to 128 contiguous rows) arrives by bulk copies; the group's
-//    environment slices are read with plain loads while those copies are in flight;
+//  * the A tile (K slices of up to 128 contiguous rows; one tensor-map box where the buffer has
+//    a row view, else one bulk copy per slice) and the group's environment slices arrive on an
+//    mbarrier, requested while the previous work item is finished;
 //  * both operands are split x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) into the K-major,
 //    non-swizzled layout the shared-memory matrix descriptors address: core matrices of 8 rows x
 //    16 bytes, K-adjacent core matrices 128 bytes apart (leading byte offset), consecutive 8-row
@@ -1362,7 +1363,8 @@ __global__ void __launch_bounds__(320) level_seg_ws_kernel(GemmDesc g, int rtile
 //    per instruction), lo*hi + hi*lo + hi*hi per K step, float32 accumulation in tensor memory
 //    (the 3xTF32 product, ~2^-21 relative per product); a group with more items than fit in
 //    the CTA's accumulator columns (at most 128) runs in several passes;
-//  * warp w reads tensor-memory lanes 32w..32w+31 (= rows) back with tcgen05.ld and stores them.
+//  * warp w reads tensor-memory lanes 32w..32w+31 (= rows) back with tcgen05.ld and writes them
+//    through its staging tile with one bulk store.
 // Every wait is bounded (2 s); after a timeout the CTA waits once more, then frees its tensor
 // memory and leaves, and the host reports TTN_ETIMEOUT.
 constexpr int kUmmaRows = 128;   // MMA M: one accumulator lane per row

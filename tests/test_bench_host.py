@@ -98,3 +98,12 @@ def test_kernel_table_orders_by_time_and_skips_phases():
     assert list(t) == ["b", "a"]
     assert t["b"] == {"ms": 15.0, "launches": 1.0, "share": 0.75}
     assert t["a"]["share"] == 0.25
+
+
+def test_source_digest_ignores_comments_and_blank_space_but_not_code():
+    a = "int f(int x) {  // doubled\n  return 2 * x; /* twice */ }\n"
+    b = "int f(int x) { return 2 * x; }"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.source_digest([a]) == bench.source_digest([b])
+    assert bench.source_digest([b]) != bench.source_digest([c])
+    assert bench._code_only('p = "a//b"; // c') == 'p = "a//b";'
