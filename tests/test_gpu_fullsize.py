@@ -137,3 +137,66 @@ def test_full_size_environments_and_heff(T, ctx, name, nodes, prec):
         for s in range(3):
             ref = N.heff_apply(tree, otn, t, [x[s] for x in blk], blk[t][s])
             assert np.abs(got[s] - ref).max() <= 10 * tol * np.abs(ref).max(), (t, s)
+
+
+# --- fitting and ALS at the benchmark size ------------------------------------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_fit_matches_oracle(T, ctx, prec):
+    """Variational fitting (Sec. II.C.2) on the 12-mode QFF, fork-4 tree, D = 24, two sweeps, of
+    a residual-like target H x_0 - 1.5 x_0 and of a combination of three states, node tensor by
+    node tensor against the oracle (same seeded states, same start, the oracle's state-diagram
+    TTNO imported; the gauge, QR with a non-negative R diagonal, is unique for full-rank nodes).
+    Tolerances as for the small trees: float64 1e-10, float32 2e-4 relative per node."""
+    from oracle import solvers as S
+    w = I.make_workload("c2")
+    tree = w.tree
+    th = T.ttn_tree_create(ctx, tree)
+    otn = N.build_ttno(tree, w.ham)
+    idt = N.identity_ttno(tree)
+    H = _import_ttno(T, ctx, th, tree, otn)
+    n = 5
+    blk = I.initial_block(tree, w.ham, w.bonds, n, seed=4, noise=1e-2)
+    X = [[x[j] for x in blk] for j in range(n)]
+    bX = T.block_from_arrays(ctx, th, w.bonds, blk)
+    out = T.ttn_block_create(ctx, th, 2, w.bonds)
+    T.ttn_block_copy_states(out, bX, [0, 3])
+    coeff = np.zeros((2 * n, 2))
+    coeff[0, 0], coeff[n + 0, 0] = 1.0, -1.5
+    coeff[n + 1, 1], coeff[n + 3, 1], coeff[n + 4, 1] = 0.3, -0.7, 0.2
+    T.ttn_recompress(ctx, coeff, [H] * n + [None] * n, [bX] * (2 * n), list(range(n)) * 2, out,
+                     n_sweeps=2, prec=prec)
+    shp = [I.node_shape(tree, w.bonds, t) for t in range(tree.n_nodes)]
+    got = T.block_to_arrays(out, shp)
+    ref0 = S.fit(tree, [(1.0, otn, X[0]), (-1.5, idt, X[0])], X[0], 2)
+    ref1 = S.fit(tree, [(0.3, idt, X[1]), (-0.7, idt, X[3]), (0.2, idt, X[4])], X[3], 2)
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    for t in range(tree.n_nodes):
+        for s, ref in ((0, ref0), (1, ref1)):
+            assert np.abs(got[t][s] - ref[t]).max() <= tol * np.abs(ref[t]).max(), (t, s)
+
+
+def test_full_size_als_matches_oracle(T, ctx):
+    """One state of the ALS preconditioner solve (H - s) y = r (Sec. II.C.3) on the 12-mode QFF,
+    fork-4 tree, D = 24, two sweeps of 10 MINRES steps with no stopping tolerance, float64,
+    against the oracle: the represented vector to 1e-8 relative (as for the small trees: the
+    rounding of the two implementations is amplified along the dependent Krylov steps)."""
+    from oracle import solvers as S
+    w = I.make_workload("c2")
+    tree = w.tree
+    th = T.ttn_tree_create(ctx, tree)
+    otn = N.build_ttno(tree, w.ham)
+    H = _import_ttno(T, ctx, th, tree, otn)
+    blk = I.initial_block(tree, w.ham, w.bonds, 1, seed=6, noise=1e-2)
+    X0 = [x[0] for x in blk]
+    bR = T.block_from_arrays(ctx, th, w.bonds, blk)
+    bY = T.block_from_arrays(ctx, th, w.bonds, blk)
+    lam0 = N.expectation(tree, otn, X0, X0) / N.overlap(tree, X0, X0)
+    shift = lam0 - 300.0
+    T.ttn_als_solve(ctx, H, np.array([shift]), bR, bY, n_sweeps=2, minres_max=10, minres_tol=0.0,
+                    prec="fp64")
+    shp = [I.node_shape(tree, w.bonds, t) for t in range(tree.n_nodes)]
+    got = [g[0] for g in T.block_to_arrays(bY, shp)]
+    ref = S.als_solve(tree, otn, shift, X0, X0, 2, 10, 0.0)
+    for t in range(tree.n_nodes):
+        assert np.abs(got[t] - ref[t]).max() <= 1e-8 * np.abs(ref[t]).max(), t
