@@ -146,8 +146,10 @@ def test_full_size_fit_matches_oracle(T, ctx, prec):
     """Variational fitting (Sec. II.C.2) on the 12-mode QFF, fork-4 tree, D = 24, two sweeps, of
     a residual-like target H x_0 - 1.5 x_0 and of a combination of three states, node tensor by
     node tensor against the oracle (same seeded states, same start, the oracle's state-diagram
-    TTNO imported; the gauge, QR with a non-negative R diagonal, is unique for full-rank nodes).
-    Tolerances as for the small trees: float64 1e-10, float32 2e-4 relative per node."""
+    TTNO imported). The states are dense random TTNS with unit node tensors, so every node is
+    full rank and the gauge (QR with a non-negative R diagonal) is unique; near-product states
+    would leave the orthogonal completion of their rank-deficient nodes free. Tolerances as
+    for the small trees: float64 1e-10, float32 2e-4 relative per node."""
     from oracle import solvers as S
     w = I.make_workload("c2")
     tree = w.tree
@@ -156,7 +158,9 @@ def test_full_size_fit_matches_oracle(T, ctx, prec):
     idt = N.identity_ttno(tree)
     H = _import_ttno(T, ctx, th, tree, otn)
     n = 5
-    blk = I.initial_block(tree, w.ham, w.bonds, n, seed=4, noise=1e-2)
+    blk = I.random_block(tree, w.bonds, n, 4)
+    for x in blk:   # unit node tensors: states of norm ~1 (float32 would overflow otherwise)
+        x /= np.linalg.norm(x.reshape(n, -1), axis=1).reshape((n,) + (1,) * (x.ndim - 1))
     X = [[x[j] for x in blk] for j in range(n)]
     bX = T.block_from_arrays(ctx, th, w.bonds, blk)
     out = T.ttn_block_create(ctx, th, 2, w.bonds)
