@@ -68,7 +68,8 @@ typedef struct ttn_envs ttn_envs;
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to issue work on,
  * or NULL for a stream owned by the context. device = -1 creates a host-only context that
- * can create trees and build, import and export TTNOs, and nothing else (no GPU needed). */
+ * can create trees and build, import and export TTNOs, and nothing else (no GPU needed).
+ * On a device, creation also prepares ttn_rayleigh_ritz_noalloc there (once per device). */
 ttn_status ttn_create(ttn_ctx** out, int device, void* cuda_stream);
 void ttn_destroy(ttn_ctx* ctx);
 /* Message of the last failing call on this context ("" if none). Valid until the next call. */
